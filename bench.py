@@ -1,0 +1,318 @@
+"""Benchmark of the Motifs-k hot path on GB300.
+
+A step is one pass of the whole path over one batch: randomise R null graphs,
+rebuild their CSRs, plan, enumerate + classify + count every connected k-set of
+the original and the R nulls in one launch, z-scores.  The default workload is
+the k=5 null-model batch (directed Chung-Lu n=1,500, m=6,000, gamma 2.2, 10%
+reciprocal, plus 256 arc-swap nulls with 10*m attempts each, seeds 1..256).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+# Root sample the CPU oracle times (k-sets whose smallest vertex is in it).
+CPU_SAMPLE = {"nullmodel_k5": (200, 232), "nullmodel_k6": (200, 220), "chunglu_k4": (0, 2000),
+              "uniform_k3": (0, 300)}
+INT32_LANES_PER_SM = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+
+
+def run_reference(args, world, rank):
+    import oracle
+
+    if rank != 0:
+        return
+    w = syn.WORKLOADS[args.workload]
+    k = w["k"]
+    g = syn.workload_graph(args.workload)
+    a, b = CPU_SAMPLE[args.workload]
+    roots = np.arange(a, min(b, g.n))
+    cores = oracle.default_threads()
+    for _ in range(args.warmup):
+        oracle.count_roots(g, k, roots)
+    times, sets = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, sets = oracle.count_roots(g, k, roots)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sets * args.steps / total
+    sample = (f"k-sets of the original graph whose smallest vertex is in [{a},{b}) "
+              f"({sets} sets per step)")
+    line = {"impl": "reference", "metric": "k-subgraphs classified/s", "value": value,
+            "unit": "subgraphs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": _config(args, w, world),
+            "cpu_baseline": {"value": value, "unit": "subgraphs/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "subgraphs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, w, world):
+    c = {"workload": args.workload, "k": w["k"], "n": w["n"], "m": w["m"],
+         "gamma": w.get("gamma"), "dmax": w.get("dmax"), "reciprocity": w.get("recip"),
+         "null_graphs": w.get("nulls", 0), "swaps_per_null": 10 * w["m"] if w.get("nulls") else 0,
+         "graphs_per_step": 1 + w.get("nulls", 0), "parallelism": f"replicas{world}",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    return c
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1804_09741_gb300 as mt
+
+    torch.cuda.set_device(local)
+    mt.load_library()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = syn.WORKLOADS[args.workload]
+    k = w["k"]
+    R = w.get("nulls", 0)
+    g = syn.workload_graph(args.workload)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    table = mt.table_build(k)
+    table_ms = 1000 * (time.perf_counter() - t0)
+    dg = mt.graph_from(g)
+    C = table.num_classes
+    seeds = (np.arange(1, R + 1) + rank * R).astype(np.uint64) if R else None
+    swaps = 10 * g.m
+
+    if R:
+        batch = mt.Batch(dg, table, R, swaps)
+        hists = torch.empty((R + 1, C), dtype=torch.int64, device="cuda")
+        z = torch.empty(C, dtype=torch.float64, device="cuda")
+
+        def step():
+            batch.run(seeds, hists, z)
+        launches_per_step = 9
+    else:
+        hists = torch.empty(C, dtype=torch.int64, device="cuda")
+
+        def step():
+            mt.count(dg, table, hists)
+        launches_per_step = 4
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    subgraphs_per_step = int(mt.to_numpy_u64(hists).astype(np.uint64).sum())
+    if R:
+        assert batch.error() == 0, "device stack overflow"
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    count_ms = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        if R:
+            count_ms.append(batch.phase_ms()[1])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    value = subgraphs_per_step * args.steps * world / (total_ms / 1000.0)
+
+    # end to end through the public API with host buffers: load the graph from
+    # host CSR, run the one-shot batch into host histograms and z-scores.
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        rp = np.ascontiguousarray(g.row_ptr, np.int32)
+        col = np.ascontiguousarray(g.col, np.int32)
+        e2e_times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            gg = mt.graph_load_csr(g.n, rp, col)
+            if R:
+                hh, zz = mt.count_batch(gg, table, seeds, swaps)
+            else:
+                hh = mt.count_host(gg, table)
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t1)
+            gg.free()
+        assert int(hh.sum()) == subgraphs_per_step
+        h2d = rp.nbytes + col.nbytes + (seeds.nbytes if R else 0)
+        d2h = (R + 1) * C * 8 + (C * 8 if R else 0)
+        e2e = {"value": subgraphs_per_step / min(e2e_times), "unit": "subgraphs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1000 * min(e2e_times)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        a, b = CPU_SAMPLE[args.workload]
+        t1 = time.perf_counter()
+        _, sets = oracle.count_roots(g, k, np.arange(a, min(b, g.n)))
+        dt = time.perf_counter() - t1
+        cpu = {"value": sets / dt, "unit": "subgraphs/s", "cores": oracle.default_threads(),
+               "kind": "oracle",
+               "sample": f"k-sets of the original graph with smallest vertex in [{a},{b}): "
+                         f"{sets} sets in {dt:.1f} s"}
+
+    peaks, src = _peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # Tops/s
+    roofline = None
+    if R and count_ms:
+        cm = statistics.mean(count_ms)
+        ops = OPS_PER_SUBGRAPH * subgraphs_per_step
+        achieved = ops / (cm / 1000.0) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "kernel": "k_count (enumerate+classify+count)", "kernel_ms": cm,
+                    "ops_per_subgraph": OPS_PER_SUBGRAPH,
+                    "peak_source": f"152 SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_mhz} MHz "
+                                   f"({src} sm_max_mhz)"}
+
+    if rank == 0:
+        line = {"metric": "k-subgraphs classified/s", "value": value, "unit": "subgraphs/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                "data": "synthetic (seeded Chung-Lu digraph and arc-swap nulls)",
+                "config": _config(args, w, world),
+                "subgraphs_per_step": subgraphs_per_step,
+                "graphs_per_s": (1 + R) * args.steps * world / (total_ms / 1000.0),
+                "table_build_ms": table_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# Algorithmic integer operations per classified subgraph in the leaf loop:
+# candidate read, relation-word read, shift + or into the key, table read,
+# histogram add.
+OPS_PER_SUBGRAPH = 6
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nullmodel_k5", choices=sorted(syn.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

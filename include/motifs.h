@@ -1,0 +1,229 @@
+/*
+ * motifs.h -- C ABI of the GB300 (sm_103a) Motifs-k library.
+ *
+ * The library counts, for k = 3..6, every weakly connected induced k-vertex
+ * subgraph of a directed graph G and groups the counts by isomorphism class,
+ * giving the histogram H_k(G) of Problem 1 ("Motifs-k", Sec. 1).  Each subgraph
+ * is classified in O(1) by looking its adjacency bits up in a precomputed
+ * isomorphism table (Sec. 3.2).  A degree-preserving arc-swap randomiser makes
+ * the null graphs of the significance step (Sec. 1, step (c)), and a batched
+ * entry point counts the original graph and R null graphs in one pass and
+ * returns per-class z-scores.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an mt_status and never aborts; no C++ exception
+ *   crosses this boundary.  Input errors are reported as MT_EINVAL before any
+ *   device work starts.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Work is enqueued on it; unless a function says it synchronises,
+ *   results are valid after the stream is synchronised.
+ * - Handles (mt_graph, mt_table, mt_batch) own device memory the library
+ *   allocated; the caller frees them with the matching *_free.  Buffers passed
+ *   in by the caller stay the caller's.  Pointers documented as "device or host"
+ *   are inspected with cudaPointerGetAttributes: a device pointer keeps the call
+ *   asynchronous, a host pointer makes the call copy and synchronise the stream.
+ * - A handle may be used by one host thread at a time.
+ * - Graphs: n vertices numbered 0..n-1 (1 <= n <= 65535), m arcs given as an
+ *   int32 CSR of out-neighbours (row_ptr[n+1], col[m]); rows may be unsorted;
+ *   self-loops, duplicate arcs, ids outside [0,n) and non-monotone row_ptr are
+ *   MT_EINVAL (Sec. 2 defines G by its arc set; the classes of Sec. 3.2 have
+ *   no diagonal, so self-loops have no place in a key).
+ * - Connectivity is weak: two vertices are adjacent when an arc joins them in
+ *   either direction (delta(v) = A(v) u B(v) u C(v), Sec. 2).
+ *
+ * Class identifiers and canonical masks
+ * -------------------------------------
+ * A k-vertex digraph on positions 0..k-1 is written as the k(k-1)-bit
+ * "canonical-layout mask": bit i*(k-1) + (j - [j > i]) is set iff the arc from
+ * position i to position j exists (the adjacency matrix of Sec. 3.2, row-major,
+ * diagonal dropped).  The canonical mask of a class is the smallest such mask
+ * over all k! orderings of its vertices.  Dense class ids 0..C-1 number the
+ * weakly connected classes in ascending order of canonical mask, C = 13, 199,
+ * 9,364 and 1,530,843 for k = 3..6 (Sec. 1 prints 1,530,842 for k = 6; the
+ * Burnside count of weakly connected 6-vertex digraphs is 1,530,843).
+ * Histograms are uint64[C] indexed by dense id; mt_table_class_masks maps ids
+ * back to canonical masks.
+ */
+#ifndef MOTIFS_H_
+#define MOTIFS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MT_OK = 0,
+  MT_EINVAL = 1,        /* bad argument or malformed graph */
+  MT_EUNSUPPORTED = 2,  /* k outside 3..6, n > 65535, or a degree too large */
+  MT_ENOMEM = 3,        /* device or pinned-host allocation failed */
+  MT_ECUDA = 4,         /* a CUDA runtime call failed */
+  MT_ETIMEOUT = 5,      /* a bounded device wait expired */
+  MT_EOVERFLOW = 6,     /* a device stack or queue bound was exceeded */
+  MT_EBUSY = 7          /* admission refused: memory budget or slots full */
+} mt_status;
+
+typedef struct mt_graph mt_graph;
+typedef struct mt_table mt_table;
+typedef struct mt_batch mt_batch;
+
+/* Text for a status code (static storage). */
+const char* mt_status_str(mt_status s);
+
+/* Last CUDA error text seen by the library on this thread ("" if none). */
+const char* mt_last_error(void);
+
+/* ----------------------------------------------------------------- graphs */
+
+/* Load a directed graph (Sec. 2: G(V,E), n = |V|, m = |E|) from a host CSR of
+ * out-neighbours.  `row_ptr` (n+1 int32) and `col` (m int32) are HOST pointers,
+ * only read during the call.  The library validates the arrays on the host,
+ * copies them into device memory it owns, then builds on the device the sorted
+ * directed CSR and the undirected neighbour CSR in which every entry carries
+ * the 2-bit relation of Sec. 2 (A: both arcs, B: v->u only, C: u->v only).
+ * Synchronises `stream` (a duplicate arc is detected on the device).
+ * Errors: MT_EINVAL (null pointers, n < 1, m < 0, row_ptr[0] != 0,
+ * row_ptr[n] != m, decreasing row_ptr, id out of range, self-loop, duplicate
+ * arc), MT_EUNSUPPORTED (n > 65535), MT_ENOMEM, MT_ECUDA.  *out is set only on
+ * MT_OK. */
+mt_status mt_graph_load_csr(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col,
+                            void* stream, mt_graph** out);
+
+/* Free a graph handle (NULL is accepted).  Synchronises the device first. */
+mt_status mt_graph_free(mt_graph* g);
+
+/* Sizes of a loaded graph: vertices, arcs, undirected edges (pairs joined by at
+ * least one arc) and the largest undirected degree d(v) = |delta(v)|.
+ * Synchronises the graph's last stream.  Any output pointer may be NULL. */
+mt_status mt_graph_info(const mt_graph* g, int32_t* n, int32_t* m, int32_t* m_undirected,
+                        int32_t* max_degree);
+
+/* Copy the sorted directed CSR back to HOST arrays row_ptr[n+1], col[m].
+ * Synchronises `stream`. */
+mt_status mt_graph_copy_csr(const mt_graph* g, int32_t* row_ptr, int32_t* col, void* stream);
+
+/* ----------------------------------------------------------------- tables */
+
+/* Build the isomorphism table ISO for subgraph size k (Sec. 3.2: every
+ * adjacency matrix of k vertices maps to the id of its class), entirely on
+ * the device: each of the 2^(k(k-1)) keys is canonicalised by the minimum over
+ * all k! vertex orderings, the connected canonical masks are ranked, and each
+ * key's slot receives its dense class id, or 0xFFFFFFFF for a disconnected
+ * pattern.  Device memory: 4 * 2^(k(k-1)) bytes (4 GiB for k = 6) plus
+ * 2^(k(k-1))/4 bytes of scratch freed before return.
+ * Key layout ("extension-order key", used by the counting kernels): the k
+ * vertices are listed in the order the enumerator adds them; position p >= 1
+ * owns the 2p bits starting at p(p-1), and within them bits 2q and 2q+1
+ * (q < p) are set iff the arcs (position q -> position p) and (position p ->
+ * position q) exist.  Synchronises `stream`.
+ * Errors: MT_EUNSUPPORTED (k outside 3..6), MT_ENOMEM, MT_ECUDA. */
+mt_status mt_table_build(int k, void* stream, mt_table** out);
+
+mt_status mt_table_free(mt_table* t);
+
+/* k of the table and the number of weakly connected classes C. */
+mt_status mt_table_k(const mt_table* t, int* k);
+mt_status mt_table_num_classes(const mt_table* t, uint32_t* out);
+
+/* Canonical masks (canonical layout, see above) of all C classes, ascending;
+ * index = dense id.  `masks` is a HOST array of C uint32.  Synchronous. */
+mt_status mt_table_class_masks(const mt_table* t, uint32_t* masks);
+
+/* Copy table slots [first, first+count) (extension-order keys) to a HOST array
+ * of uint32 dense ids (0xFFFFFFFF = disconnected).  Synchronous.
+ * Errors: MT_EINVAL when the range leaves [0, 2^(k(k-1))). */
+mt_status mt_table_entries(const mt_table* t, uint64_t first, uint64_t count, uint32_t* ids);
+
+/* ----------------------------------------------------------------- counting */
+
+/* H_k(G) (Problem 1, Sec. 1) with k = the table's k: for every dense class id c,
+ * hist[c] = number of vertex sets S, |S| = k, with G[S] weakly connected and of
+ * class c.  `hist` is uint64[C], device or host; it is overwritten.  Every
+ * connected set is produced exactly once by the extension enumerator (root =
+ * smallest vertex, extension by exclusive neighbours), its adjacency bits are
+ * gathered from the labelled neighbour rows (the row-scan strategy of Sec. 3.1)
+ * and classified by one table read (Sec. 3.2).  n < k gives all zeros.
+ * The call may grow device scratch memory held by the graph handle.
+ * Errors: MT_EINVAL (null handle or hist), MT_EUNSUPPORTED (degree bound of the
+ * device stack exceeded), MT_EOVERFLOW (device stack overflow detected, the
+ * histogram is then invalid), MT_ENOMEM, MT_ECUDA. */
+mt_status mt_count(const mt_graph* g, const mt_table* t, uint64_t* hist, void* stream);
+
+/* H_k restricted to the connected k-sets whose smallest vertex lies in
+ * [root_begin, root_end) (clamped to [0, n)).  Sets are assigned to their
+ * smallest vertex, so histograms of disjoint root ranges add up to mt_count's:
+ * the unit by which work can be split between calls or devices, and by which
+ * a CPU reference can check a large graph on a sample of roots.  Arguments,
+ * memory and errors as mt_count. */
+mt_status mt_count_roots(const mt_graph* g, const mt_table* t, int32_t root_begin,
+                         int32_t root_end, uint64_t* hist, void* stream);
+
+/* Same as mt_count with explicit tuning: `split_cost` is the estimated work
+ * (in classified subgraphs) above which a first-level extension branch is
+ * split into second-level work items, and the size of first-level items
+ * (0 = automatic: the total estimate spread over 24 items per resident warp);
+ * `warps_per_block` is the block size in warps (0 = automatic, else 1..16). */
+mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist, double split_cost,
+                         int warps_per_block, void* stream);
+
+/* Diagnostics of the last counting call on this graph: number of work items
+ * the planner made, the device error word (0 = fine; non-zero = stack or queue
+ * overflow, the histogram is invalid) and the enumerator's time in ms (device
+ * events around planner + enumerator).  Waits for that call to finish.  With a
+ * device histogram, mt_count does not synchronise, so overflow is reported
+ * only here. */
+mt_status mt_count_stats(const mt_graph* g, uint64_t* items, uint32_t* err, float* ms);
+
+/* ----------------------------------------------------------------- null model */
+
+/* One null graph by degree-preserving directed arc swaps (Sec. 1 step (c); the
+ * paper names no randomisation model, the reading is the switch of Milo et al.):
+ * attempt t = 0..swaps-1 draws arc positions e1, e2 from SplitMix64 outputs 2t
+ * and 2t+1 of `seed` (index = floor(r * m / 2^64)); arcs (a->b), (c->d) become
+ * (a->d), (c->b) unless e1 == e2, a == c, b == d, a == d, c == b, or a new arc
+ * already exists; attempts run in order, one after another.  In- and
+ * out-degrees are preserved.  The result is a new graph handle (sorted CSR and
+ * undirected CSR rebuilt on the device).  Synchronises `stream`.
+ * Errors: MT_EINVAL, MT_ENOMEM, MT_ECUDA. */
+mt_status mt_randomize(const mt_graph* src, uint64_t seed, uint64_t swaps, void* stream,
+                       mt_graph** out);
+
+/* Batched null model: the original graph plus R null graphs (seeds[r], `swaps`
+ * attempts each) counted in one persistent launch.  The handle pre-allocates
+ * every buffer; the first mt_batch_run captures the whole step (randomise,
+ * rebuild, plan, count, z-scores) into a CUDA graph on `stream` and later runs
+ * replay it.  R >= 1. */
+mt_status mt_batch_create(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
+                          mt_batch** out);
+mt_status mt_batch_free(mt_batch* b);
+
+/* Run a batch.  `seeds`: HOST array of R uint64.  `hists`: uint64[(R+1)*C]
+ * (row 0 = original graph, row r = null graph r), device or host.  `z`:
+ * double[C], device or host, may be NULL: the z-score of each class,
+ * z = (H(G) - mu) / sigma with mu and sigma the mean and population standard
+ * deviation of the R null counts in float64 (sigma = 0: z = 0 if H(G) == mu,
+ * else +-inf).  Errors as mt_count. */
+mt_status mt_batch_run(mt_batch* b, const uint64_t* seeds, uint64_t* hists, double* z,
+                       void* stream);
+
+/* Device-side timing of the last mt_batch_run's phases, milliseconds:
+ * out[0] randomise + rebuild, out[1] plan + count, out[2] z-scores. */
+mt_status mt_batch_phase_ms(const mt_batch* b, float out[3]);
+
+/* Error word of the last mt_batch_run's counting launch (0 = fine; non-zero =
+ * stack or queue overflow, the histograms are invalid).  Synchronises the
+ * device. */
+mt_status mt_batch_error(const mt_batch* b, uint32_t* err);
+
+/* One-shot form of the batch: create, run, free. */
+mt_status mt_count_batch(const mt_graph* g, const mt_table* t, const uint64_t* seeds, int R,
+                         uint64_t swaps, uint64_t* hists, double* z, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOTIFS_H_ */

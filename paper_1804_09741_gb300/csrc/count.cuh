@@ -1,0 +1,51 @@
+// Enumerate-and-classify launch (K2) and its planner.
+#pragma once
+
+#include "graph.cuh"
+
+namespace mt {
+
+const uint32_t* table_device(const mt_table* t);
+int table_k(const mt_table* t);
+uint32_t table_classes(const mt_table* t);
+
+// Host-side shape of one counting launch over G graphs.
+struct CountPlan {
+  int K = 0;
+  int G = 0;
+  int nmax = 0;             // largest n among the graphs
+  int dmax = 0;             // bound on every undirected degree
+  int64_t fwd_bound = 0;    // bound on the number of forward entries, all graphs
+  int64_t entry_stride = 0; // per-graph stride of the planner's entry arrays (>= max nu)
+  int warps_per_block = 0;
+  int blocks = 0;
+  bool lab_smem = true;
+  int cap = 0;              // stack entries per warp
+  size_t smem_bytes = 0;
+  uint64_t items_max = 0;
+  double split_cost = 0.0;  // 0 = automatic
+  uint32_t classes = 0;
+  size_t ws_bytes = 0;
+  // workspace offsets
+  size_t off_hdr = 0, off_est = 0, off_cnt = 0, off_items = 0, off_lab = 0;
+};
+
+// Fill in the launch shape and the workspace size.  `fwd_bound` is a bound on
+// the total number of forward entries (sum of undirected edges) of the G graphs.
+mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
+                          int64_t entry_stride, uint32_t classes, double split_cost,
+                          int warps_per_block);
+
+// Enqueue planner + enumerator.  `graphs` is a device array of G DevGraph whose
+// hist pointers are already zeroed (the launch adds into them).  Roots in
+// [root_begin, root_end) only.  No host synchronisation, no allocation.
+mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
+                        const uint32_t* table, int32_t root_begin, int32_t root_end,
+                        cudaStream_t s);
+
+// Read the launch's error word and item count from the workspace (device
+// pointers into `ws`).
+uint32_t* count_err_ptr(const CountPlan& p, void* ws);
+uint32_t* count_nitems_ptr(const CountPlan& p, void* ws);
+
+}  // namespace mt
