@@ -137,10 +137,11 @@ def run_reference(args, world, rank):
 
 
 def _config(args, w, world):
+    nulls = w.get("nulls", 0) if args.nulls is None else args.nulls
     c = {"workload": args.workload, "k": w["k"], "n": w["n"], "m": w["m"],
          "gamma": w.get("gamma"), "dmax": w.get("dmax"), "reciprocity": w.get("recip"),
-         "null_graphs": w.get("nulls", 0), "swaps_per_null": 10 * w["m"] if w.get("nulls") else 0,
-         "graphs_per_step": 1 + w.get("nulls", 0), "parallelism": f"replicas{world}",
+         "null_graphs": nulls, "swaps_per_null": 10 * w["m"] if nulls else 0,
+         "graphs_per_step": 1 + nulls, "parallelism": f"replicas{world}",
          "l2": "flushed between timed steps (256 MiB write)"}
     return c
 
@@ -161,7 +162,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl")
     w = syn.WORKLOADS[args.workload]
     k = w["k"]
-    R = w.get("nulls", 0)
+    R = w.get("nulls", 0) if args.nulls is None else args.nulls
     g = syn.workload_graph(args.workload)
     stream = torch.cuda.current_stream()
 
@@ -186,7 +187,7 @@ def run_ours(args, world, rank, local):
 
         def step():
             mt.count(dg, table, hists)
-        launches_per_step = 4
+        launches_per_step = 5
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -306,6 +307,9 @@ def main():
     ap.add_argument("--workload", default="nullmodel_k5", choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nulls", type=int, default=None,
+                    help="number of null graphs (default: the workload's); smaller values make "
+                         "the small cases profiled under ncu, recorded in config")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":
