@@ -169,6 +169,28 @@ mt_status mt_count_roots(const mt_graph* g, const mt_table* t, int32_t root_begi
 mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist, double split_cost,
                          int warps_per_block, void* stream);
 
+/* mt_count for programs that must not allocate GPU memory while they run: a
+ * service that reserves its whole device-memory budget at start-up (its own
+ * pool, or a framework's caching allocator, owns every byte), or a
+ * latency-sensitive loop that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the device.  mt_count grows scratch memory on the graph handle;
+ * this call instead takes the planner's and the work queue's scratch from one
+ * fixed 8 MiB array compiled into the library, reserved on every GPU that loads
+ * the library until the process exits, and allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library call).  The paper has no counterpart: it
+ * is a deployment variant of the same count.
+ * - `hist` must be device memory (uint64[C]); it is overwritten.  Results equal
+ *   mt_count's.  The call is asynchronous on `stream`.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - All calls share the one array: calls that overlap on the GPU (other
+ *   streams or host threads) race and give wrong counts.  Serialise them.
+ * - Errors: MT_EINVAL (null handle, or hist not device memory),
+ *   MT_EUNSUPPORTED when the graph needs more scratch than the array holds
+ *   (mt_last_error() gives both sizes; use mt_count), MT_ECUDA. */
+mt_status mt_count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* hist, void* stream);
+
 /* Diagnostics of the last counting call on this graph: number of work items
  * the planner made, the device error word (0 = fine; non-zero = stack or queue
  * overflow, the histogram is invalid) and the enumerator's time in ms (device

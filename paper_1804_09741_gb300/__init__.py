@@ -49,6 +49,7 @@ SIGNATURES = {
     "mt_count_roots": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
     "mt_count_tuned": (ctypes.c_int, [_vp, _vp, _vp, _f64, ctypes.c_int, _vp]),
     "mt_count_stats": (ctypes.c_int, [_vp, _P(_u64), _P(_u32), _P(ctypes.c_float)]),
+    "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_randomize": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_batch_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(_vp)]),
     "mt_batch_free": (ctypes.c_int, [_vp]),
@@ -243,6 +244,15 @@ def count_tuned(g: Graph, t: Table, split_cost: float = 0.0, warps_per_block: in
     out = _dev_hist(t, out)
     _check(_lib.mt_count_tuned(g.handle, t.handle, out.data_ptr(), float(split_cost),
                                int(warps_per_block), _stream(stream)), "mt_count_tuned")
+    return out
+
+
+def count_noalloc(g: Graph, t: Table, out=None, stream=None):
+    """mt_count without any GPU allocation inside the call (fixed scratch in the
+    library; calls must not overlap on the GPU).  ``out`` must be on the GPU."""
+    out = _dev_hist(t, out)
+    _check(_lib.mt_count_noalloc(g.handle, t.handle, out.data_ptr(), _stream(stream)),
+           "mt_count_noalloc")
     return out
 
 
