@@ -153,6 +153,7 @@ def run_ours(args, world, rank, local):
     import torch
 
     import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300 import shard
 
     torch.cuda.set_device(local)
     mt.load_library()
@@ -171,7 +172,7 @@ def run_ours(args, world, rank, local):
     table_ms = 1000 * (time.perf_counter() - t0)
     dg = mt.graph_from(g)
     C = table.num_classes
-    seeds = (np.arange(1, R + 1) + rank * R).astype(np.uint64) if R else None
+    seeds = shard.rank_seeds(R, rank) if R else None
     swaps = 10 * g.m
 
     if R:

@@ -165,7 +165,7 @@ mt_status mt_count_roots(const mt_graph* g, const mt_table* t, int32_t root_begi
  * (in classified subgraphs) above which a first-level extension branch is
  * split into second-level work items, and the size of first-level items
  * (0 = automatic: the total estimate spread over 24 items per resident warp);
- * `warps_per_block` is the block size in warps (0 = automatic, else 1..16). */
+ * `warps_per_block` is the block size in warps (0 = automatic, else 1..32). */
 mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist, double split_cost,
                          int warps_per_block, void* stream);
 

@@ -29,6 +29,7 @@
 // branches, (graph, root, branch, second-level choice range); a planner sizes
 // them from per-branch cost estimates and warps take them from a global queue.
 #include <algorithm>
+#include <type_traits>
 
 #include "count.cuh"
 
@@ -44,7 +45,7 @@ struct Hdr {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kTargetItemsPerWarp = 24;
-constexpr int kMaxWarpsPerBlock = 16;
+constexpr int kMaxWarpsPerBlock = 32;
 
 __device__ __forceinline__ float choose_f(int x, int r) {
   if (x < r) return 0.f;
@@ -201,10 +202,15 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int32_t* data, int count) 
 
 // ------------------------------------------------------------------ enumerator
 
+// Relation words: 2 bits per earlier position, k-1 positions -> 8 bits for k <= 5.
+template <int K>
+using LabT = typename std::conditional<(K <= 5), uint8_t, uint16_t>::type;
+
+template <int K>
 struct WarpCtx {
-  const int32_t* __restrict__ urow;
-  const uint32_t* __restrict__ ucol;
-  uint16_t* lab;
+  const int32_t* urow;   // shared-memory copy of the graph or global memory
+  const uint32_t* ucol;
+  LabT<K>* lab;
   uint16_t* buf;
   int cap;
   int root;
@@ -212,12 +218,22 @@ struct WarpCtx {
   uint32_t* err;
 };
 
-// Push w at position p: OR its relation bits into lab[] of its neighbours
-// above the root and append the exclusive ones at stack index e.  Returns the
-// new end of the candidate list.
-__device__ __forceinline__ int push_vertex(const WarpCtx& w, int x, int p, int e) {
-  const int rs = __ldg(&w.urow[x]), re = __ldg(&w.urow[x + 1]);
-  const int start = (re - rs > 32) ? first_above(w.ucol, rs, re, w.root) : rs;
+// First index in sorted packed entries [lo, hi) whose vertex is > x.
+__device__ __forceinline__ int first_above_p(const uint32_t* ucol, int lo, int hi, int x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((int)(ucol[mid] & kVertexMask) > x) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Push x at position p: OR its relation bits into lab[] of its neighbours above
+// the root and append the exclusive ones (relation word was zero) at stack
+// index e.  Returns the new end of the candidate list.
+template <int K>
+__device__ __forceinline__ int push_vertex(const WarpCtx<K>& w, int x, int p, int e) {
+  const int rs = w.urow[x], re = w.urow[x + 1];
+  const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
   const unsigned lt = (1u << w.lane) - 1u;
   int cnt = 0;
   for (int b = start; b < re; b += 32) {
@@ -225,11 +241,11 @@ __device__ __forceinline__ int push_vertex(const WarpCtx& w, int x, int p, int e
     bool ex = false;
     int u = 0;
     if (i < re) {
-      const uint32_t ent = __ldg(&w.ucol[i]);
+      const uint32_t ent = w.ucol[i];
       u = (int)(ent & kVertexMask);
       if (u > w.root) {
-        const uint16_t old = w.lab[u];
-        w.lab[u] = (uint16_t)(old | ((ent >> 30) << (2 * p)));
+        const LabT<K> old = w.lab[u];
+        w.lab[u] = (LabT<K>)(old | ((ent >> 30) << (2 * p)));
         ex = (old == 0);
       }
     }
@@ -247,193 +263,247 @@ __device__ __forceinline__ int push_vertex(const WarpCtx& w, int x, int p, int e
 }
 
 // Pop the vertex x at position p: clear its relation bits again.
-__device__ __forceinline__ void pop_vertex(const WarpCtx& w, int x, int p) {
-  const int rs = __ldg(&w.urow[x]), re = __ldg(&w.urow[x + 1]);
-  const int start = (re - rs > 32) ? first_above(w.ucol, rs, re, w.root) : rs;
-  const uint16_t clear = (uint16_t)~(3u << (2 * p));
+template <int K>
+__device__ __forceinline__ void pop_vertex(const WarpCtx<K>& w, int x, int p) {
+  const int rs = w.urow[x], re = w.urow[x + 1];
+  const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
+  const LabT<K> clear = (LabT<K>)~(3u << (2 * p));
   for (int b = start; b < re; b += 32) {
     const int i = b + w.lane;
     if (i < re) {
-      const int u = (int)(__ldg(&w.ucol[i]) & kVertexMask);
+      const int u = (int)(w.ucol[i] & kVertexMask);
       if (u > w.root) w.lab[u] &= clear;
     }
   }
   __syncwarp();
 }
 
-template <int K, bool LAB_SMEM>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
-    k_count(const DevGraph* __restrict__ graphs, const Item* __restrict__ items,
-            const int32_t* n_items_p, uint64_t items_max, Hdr* hdr,
-            const uint32_t* __restrict__ table, uint16_t* lab_global, int nmax, int cap,
-            uint32_t classes, int lab_bytes, int buf_bytes, int hist_bytes) {
+struct CountArgs {
+  const DevGraph* graphs;
+  const Item* items;
+  const int32_t* item_off;   // scanned item counts: graph g owns [item_off[g*nmax], item_off[(g+1)*nmax])
+  uint32_t* qhead;           // per-graph queue heads
+  Hdr* hdr;
+  const uint32_t* table;
+  void* lab_global;
+  int G, nmax, nu_cap, cap;
+  uint32_t classes;
+  int graph_bytes, hist_bytes, lab_bytes, buf_bytes;
+};
+
+// Persistent enumerator.  A thread block works on one graph at a time: its
+// warps take that graph's items from the graph's queue; when the queue is
+// empty the block flushes its shared histogram, picks the next graph that still
+// has items and (GC) copies that graph's CSR into shared memory.
+template <int K, bool GC, bool LS>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int per_warp = (LAB_SMEM ? lab_bytes : 0) + buf_bytes + hist_bytes;
-  unsigned char* mine = smem + (size_t)wid * per_warp;
-  uint16_t* lab = LAB_SMEM ? (uint16_t*)mine
-                           : lab_global + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * nmax;
-  uint16_t* buf = (uint16_t*)(mine + (LAB_SMEM ? lab_bytes : 0));
-  uint32_t* whist = (uint32_t*)(mine + (LAB_SMEM ? lab_bytes : 0) + buf_bytes);
-  if (LAB_SMEM)
-    for (int i = lane; i < nmax; i += 32) lab[i] = 0;
-  if (K <= 4)
-    for (int i = lane; i < (int)classes; i += 32) whist[i] = 0;
-  __syncwarp();
+  __shared__ int s_cur_g;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  unsigned char* sp = smem;
+  int32_t* s_urow = (int32_t*)sp;
+  uint32_t* s_ucol = (uint32_t*)(sp + (GC ? ((a.nmax + 1) * 4 + 15) / 16 * 16 : 0));
+  sp += a.graph_bytes;
+  uint32_t* s_hist = (uint32_t*)sp;
+  sp += a.hist_bytes;
+  unsigned char* mine = sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes);
+  LabT<K>* lab = LS ? (LabT<K>*)mine
+                    : (LabT<K>*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.nmax;
+  uint16_t* buf = (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
+  const uint32_t C = a.classes;
 
-  const uint64_t nitems = min((uint64_t)(uint32_t)*n_items_p, items_max);
-  int cur_g = -1;
-  unsigned long long* cur_hist = nullptr;
-  uint64_t pending = 0;
+  if (LS)
+    for (int i = lane; i < a.nmax; i += 32) lab[i] = 0;
+  if (K <= 5)
+    for (int i = tid; i < (int)C; i += blockDim.x) s_hist[i] = 0;
+  if (tid == 0) s_cur_g = (int)(((int64_t)blockIdx.x * a.G) / gridDim.x);
+  __syncthreads();
 
-  WarpCtx w;
+  WarpCtx<K> w;
   w.lab = lab;
   w.buf = buf;
-  w.cap = cap;
+  w.cap = a.cap;
   w.lane = lane;
-  w.err = &hdr->err;
+  w.err = &a.hdr->err;
 
-  auto flush = [&]() {
-    for (int i = lane; i < (int)classes; i += 32) {
-      const uint32_t x = whist[i];
-      if (x) {
-        atomicAdd(&cur_hist[i], (unsigned long long)x);
-        whist[i] = 0;
-      }
-    }
-    __syncwarp();
-    pending = 0;
-  };
-
-  while (true) {
-    uint32_t idx = 0;
-    if (lane == 0) idx = atomicAdd(&hdr->head, 1u);
-    idx = __shfl_sync(kFull, idx, 0);
-    if (idx >= nitems) break;
-    const Item it = items[idx];
-    const DevGraph* Gp = graphs + it.g;
-    if ((int)it.g != cur_g) {
-      if (K <= 4 && cur_g >= 0) flush();
-      cur_g = (int)it.g;
-      cur_hist = Gp->hist;
+  int g = s_cur_g;
+  while (g >= 0) {
+    const DevGraph* Gp = a.graphs + g;
+    if (GC) {
+      const int n = Gp->n, nu = Gp->nu;
+      for (int i = tid; i <= n; i += blockDim.x) s_urow[i] = Gp->urow[i];
+      for (int i = tid; i < nu; i += blockDim.x) s_ucol[i] = Gp->ucol[i];
+      w.urow = s_urow;
+      w.ucol = s_ucol;
+    } else {
       w.urow = Gp->urow;
       w.ucol = Gp->ucol;
     }
-    const int v = (int)it.root;
-    w.root = v;
-    const int re = __ldg(&w.urow[v + 1]);
-    const int f = __ldg(&w.urow[v]) + __ldg(&Gp->ufwd[v]);
-    const int dplus = re - f;
-    const int j1a = it.j1a, j1b = it.j1b;
-    // push the root at position 0: every forward neighbour gets its relation
-    // bits; candidates j1a.. are copied to the stack.
-    for (int b = f; b < re; b += 32) {
-      const int i = b + lane;
-      if (i < re) {
-        const uint32_t ent = __ldg(&w.ucol[i]);
-        const int u = (int)(ent & kVertexMask);
-        lab[u] |= (uint16_t)(ent >> 30);
-        const int q = i - f - j1a;
-        if (q >= 0) buf[q] = (uint16_t)u;
+    __syncthreads();
+    unsigned long long* ghist = Gp->hist;
+    const int32_t* ufwd = Gp->ufwd;
+    const int ib = a.item_off[(int64_t)g * a.nmax];
+    const int ie = a.item_off[(int64_t)(g + 1) * a.nmax];
+
+    // Add `cnt` subgraphs of class `id` (called by one lane per group).
+    auto hadd = [&](uint32_t id, uint32_t cnt) {
+      if (id >= C) {
+        atomicOr(w.err, kErrStackOverflow);
+        return;
       }
-    }
-    __syncwarp();
-    int s_c = 0, s_ce = 0, s_e = 0, s_vert = 0;
-    uint32_t s_key = 0;
-    if (lane == 1) {
-      s_c = 0;
-      s_ce = j1b - j1a;
-      s_e = dplus - j1a;
-    }
-    if (lane == 0) s_vert = v;
-    const bool has2 = it.b2 != 0xFFFF;
-    int L = 1;
-    while (true) {
-      const int c = __shfl_sync(kFull, s_c, L);
-      const int ce = __shfl_sync(kFull, s_ce, L);
-      const int e = __shfl_sync(kFull, s_e, L);
-      const uint32_t key = __shfl_sync(kFull, s_key, L);
-      if (L == K - 1) {
-        // leaves: every remaining candidate completes a k-set
-        for (int b = c; b < e; b += 32) {
-          const int i = b + lane;
-          const bool valid = i < e;
-          uint32_t id = kNoClass;
-          if (valid) {
-            const int u = buf[i];
-            const uint32_t k2 = key | ((uint32_t)lab[u] << ((K - 1) * (K - 2)));
-            id = __ldg(&table[k2]);
-          }
-          if (K <= 4) {
-            if (valid) {
-              if (id < classes) atomicAdd(&whist[id], 1u);
-              else atomicOr(w.err, kErrStackOverflow);
-            }
-          } else {
-            const unsigned act = __ballot_sync(kFull, valid);
-            if (valid) {
-              const unsigned peers = __match_any_sync(act, id);
-              if (lane == __ffs(peers) - 1) {
-                if (id < classes) atomicAdd(&cur_hist[id], (unsigned long long)__popc(peers));
-                else atomicOr(w.err, kErrStackOverflow);
-              }
-            }
-          }
+      if (K <= 5) {
+        const uint32_t old = atomicAdd(&s_hist[id], cnt);
+        if (old < 0x80000000u && old + cnt >= 0x80000000u) {
+          // spill 2^31 to the graph's 64-bit counter so the 32-bit one never wraps
+          atomicSub(&s_hist[id], 0x80000000u);
+          atomicAdd(&ghist[id], 0x80000000ull);
         }
-        if (K <= 4) pending += (uint64_t)(e > c ? e - c : 0);
-        L -= 1;
-        pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
-        continue;
-      }
-      if (c < ce) {
-        const int x = buf[c];
-        if (lane == L) s_c = c + 1;
-        const uint32_t nkey = key | ((uint32_t)lab[x] << (L * (L - 1)));
-        const int ne = push_vertex(w, x, L, e);
-        if (lane == L) s_vert = x;
-        if (lane == L + 1) {
-          s_c = c + 1;
-          s_ce = ne;
-          s_e = ne;
-          s_key = nkey;
-        }
-        if (L == 1 && has2 && lane == 2) {
-          s_c = c + 1 + it.a2;
-          s_ce = min(c + 1 + (int)it.b2, ne);
-        }
-        L += 1;
       } else {
-        if (L == 1) break;
-        L -= 1;
-        pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
+        atomicAdd(&ghist[id], (unsigned long long)cnt);
+      }
+    };
+
+    while (true) {
+      uint32_t idx = 0;
+      if (lane == 0) idx = atomicAdd(&a.qhead[g], 1u);
+      idx = __shfl_sync(kFull, idx, 0);
+      const int64_t pos = (int64_t)ib + idx;
+      if (pos >= ie) break;
+      const Item it = a.items[pos];
+      const int v = (int)it.root;
+      w.root = v;
+      const int re = w.urow[v + 1];
+      const int f = w.urow[v] + __ldg(&ufwd[v]);
+      const int dplus = re - f;
+      const int j1a = it.j1a, j1b = it.j1b;
+      // push the root at position 0: every forward neighbour gets its relation
+      // bits; candidates j1a.. go to the stack.
+      for (int b = f; b < re; b += 32) {
+        const int i = b + lane;
+        if (i < re) {
+          const uint32_t ent = w.ucol[i];
+          const int u = (int)(ent & kVertexMask);
+          lab[u] |= (LabT<K>)(ent >> 30);
+          const int q = i - f - j1a;
+          if (q >= 0) buf[q] = (uint16_t)u;
+        }
+      }
+      __syncwarp();
+      int s_c = 0, s_ce = 0, s_e = 0, s_vert = 0;
+      uint32_t s_key = 0;
+      if (lane == 1) {
+        s_c = 0;
+        s_ce = j1b - j1a;
+        s_e = dplus - j1a;
+      }
+      if (lane == 0) s_vert = v;
+      const bool has2 = it.b2 != 0xFFFF;
+      int L = 1;
+      while (true) {
+        const int c = __shfl_sync(kFull, s_c, L);
+        const int ce = __shfl_sync(kFull, s_ce, L);
+        const int e = __shfl_sync(kFull, s_e, L);
+        const uint32_t key = __shfl_sync(kFull, s_key, L);
+        if (L == K - 1) {
+          // leaves: every remaining candidate completes a k-set.  Leaves with
+          // the same relation word to the k-1 chosen vertices lie in the same
+          // cell of the partition of the set's neighbourhood (Sec. 2) and so in
+          // the same class: one lane per cell reads the table and adds the
+          // cell's size.  Two batches of 32 are in flight.
+          for (int b = c; b < e; b += 64) {
+            const int i0 = b + lane, i1 = b + 32 + lane;
+            const bool v0 = i0 < e, v1 = i1 < e;
+            const uint32_t l0 = v0 ? (uint32_t)lab[buf[i0]] : 0xFFFFFFFFu;
+            const uint32_t l1 = v1 ? (uint32_t)lab[buf[i1]] : 0xFFFFFFFFu;
+            const unsigned p0 = __match_any_sync(kFull, l0);
+            const unsigned p1 = __match_any_sync(kFull, l1);
+            const bool lead0 = v0 && lane == __ffs(p0) - 1;
+            const bool lead1 = v1 && lane == __ffs(p1) - 1;
+            uint32_t id0 = kNoClass, id1 = kNoClass;
+            if (lead0) id0 = __ldg(&a.table[key | (l0 << ((K - 1) * (K - 2)))]);
+            if (lead1) id1 = __ldg(&a.table[key | (l1 << ((K - 1) * (K - 2)))]);
+            if (lead0) hadd(id0, __popc(p0));
+            if (lead1) hadd(id1, __popc(p1));
+          }
+          L -= 1;
+          pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+          continue;
+        }
+        if (c < ce) {
+          const int x = buf[c];
+          if (lane == L) s_c = c + 1;
+          const uint32_t nkey = key | ((uint32_t)lab[x] << (L * (L - 1)));
+          const int ne = push_vertex<K>(w, x, L, e);
+          if (lane == L) s_vert = x;
+          if (lane == L + 1) {
+            s_c = c + 1;
+            s_ce = ne;
+            s_e = ne;
+            s_key = nkey;
+          }
+          if (L == 1 && has2 && lane == 2) {
+            s_c = c + 1 + it.a2;
+            s_ce = min(c + 1 + (int)it.b2, ne);
+          }
+          L += 1;
+        } else {
+          if (L == 1) break;
+          L -= 1;
+          pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+        }
+      }
+      // pop the root
+      for (int b = f; b < re; b += 32) {
+        const int i = b + lane;
+        if (i < re) lab[w.ucol[i] & kVertexMask] &= (LabT<K>)~3u;
+      }
+      __syncwarp();
+    }
+    // this graph's queue is empty: flush, then move to a graph with items left
+    __syncthreads();
+    if (K <= 5) {
+      for (int i = tid; i < (int)C; i += blockDim.x) {
+        const uint32_t x = s_hist[i];
+        if (x) {
+          atomicAdd(&ghist[i], (unsigned long long)x);
+          s_hist[i] = 0;
+        }
       }
     }
-    // pop the root
-    for (int b = f; b < re; b += 32) {
-      const int i = b + lane;
-      if (i < re) lab[__ldg(&w.ucol[i]) & kVertexMask] &= (uint16_t)~3u;
+    if (tid == 0) {
+      int next = -1;
+      for (int t = 1; t <= a.G; ++t) {
+        const int g2 = (g + t) % a.G;
+        const int n2 = a.item_off[(int64_t)(g2 + 1) * a.nmax] - a.item_off[(int64_t)g2 * a.nmax];
+        if ((int)*(volatile uint32_t*)&a.qhead[g2] < n2) {
+          next = g2;
+          break;
+        }
+      }
+      s_cur_g = next;
     }
-    __syncwarp();
-    if (K <= 4 && pending > (1ull << 30)) flush();
+    __syncthreads();
+    g = s_cur_g;
   }
-  if (K <= 4 && cur_g >= 0) flush();
 }
 
 // ------------------------------------------------------------------ host side
 
 static size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-template <int K, bool LS>
-static const void* count_kernel() {
-  return (const void*)k_count<K, LS>;
+template <int K>
+static const void* pick_kernel_k(bool gc, bool ls) {
+  if (gc) return ls ? (const void*)k_count<K, true, true> : (const void*)k_count<K, true, false>;
+  return ls ? (const void*)k_count<K, false, true> : (const void*)k_count<K, false, false>;
 }
 
-static const void* pick_kernel(int K, bool ls) {
+static const void* pick_kernel(int K, bool gc, bool ls) {
   switch (K) {
-    case 3: return ls ? count_kernel<3, true>() : count_kernel<3, false>();
-    case 4: return ls ? count_kernel<4, true>() : count_kernel<4, false>();
-    case 5: return ls ? count_kernel<5, true>() : count_kernel<5, false>();
-    default: return ls ? count_kernel<6, true>() : count_kernel<6, false>();
+    case 3: return pick_kernel_k<3>(gc, ls);
+    case 4: return pick_kernel_k<4>(gc, ls);
+    case 5: return pick_kernel_k<5>(gc, ls);
+    default: return pick_kernel_k<6>(gc, ls);
   }
 }
 
@@ -451,43 +521,63 @@ mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_
   p->split_cost = split_cost;
   p->cap = (K - 1) * std::max(dmax, 1) + 32;
   if (p->cap > 65535) return MT_EUNSUPPORTED;
-  const size_t lab_bytes = round16((size_t)nmax * 2);
+  p->nu_cap = (int)p->entry_stride;
+  const size_t lab_bytes = round16((size_t)nmax * (K <= 5 ? 1 : 2));
   const size_t buf_bytes = round16((size_t)p->cap * 2);
-  const size_t hist_bytes = K <= 4 ? round16((size_t)classes * 4) : 0;
+  const size_t hist_bytes = K <= 5 ? round16((size_t)classes * 4) : 0;
+  const size_t graph_bytes = round16((size_t)(nmax + 1) * 4) + round16((size_t)p->nu_cap * 4);
   int dev = 0, sms = 0, max_smem = 0;
   MT_CUDA_TRY(cudaGetDevice(&dev));
   MT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   MT_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t budget = (size_t)max_smem - 1024;
-  int wpb = warps_per_block > 0 ? std::min(warps_per_block, kMaxWarpsPerBlock) : kMaxWarpsPerBlock;
-  bool ls = true;
-  while (wpb > 1 && (size_t)wpb * (lab_bytes + buf_bytes + hist_bytes) > budget) wpb /= 2;
-  if ((size_t)wpb * (lab_bytes + buf_bytes + hist_bytes) > budget || (warps_per_block == 0 && wpb < 8)) {
-    ls = false;
-    wpb = warps_per_block > 0 ? std::min(warps_per_block, kMaxWarpsPerBlock) : kMaxWarpsPerBlock;
-    while (wpb > 1 && (size_t)wpb * (buf_bytes + hist_bytes) > budget) wpb /= 2;
-    if ((size_t)wpb * (buf_bytes + hist_bytes) > budget) return MT_EUNSUPPORTED;
+  const int want = warps_per_block > 0 ? std::min(warps_per_block, kMaxWarpsPerBlock)
+                                       : kMaxWarpsPerBlock;
+  // Preference: graph copy and relation words in shared memory with >= 16 warps,
+  // then relation words only, then graph only, then neither.
+  struct Opt { bool gc, ls; };
+  const Opt opts[4] = {{true, true}, {false, true}, {true, false}, {false, false}};
+  bool found = false;
+  for (int pass = 0; pass < 2 && !found; ++pass) {
+    const int min_w = pass == 0 ? std::min(want, 16) : 1;
+    for (const Opt& o : opts) {
+      const size_t fixed = (o.gc ? graph_bytes : 0) + hist_bytes;
+      const size_t per = (o.ls ? lab_bytes : 0) + buf_bytes;
+      int w = want;
+      while (w > min_w && fixed + (size_t)w * per > budget) --w;
+      if (fixed + (size_t)w * per <= budget) {
+        p->gcache = o.gc;
+        p->lab_smem = o.ls;
+        p->warps_per_block = w;
+        p->smem_bytes = fixed + (size_t)w * per;
+        found = true;
+        break;
+      }
+    }
   }
-  p->lab_smem = ls;
-  p->warps_per_block = wpb;
-  p->smem_bytes = (size_t)wpb * ((ls ? lab_bytes : 0) + buf_bytes + hist_bytes);
-  const void* kern = pick_kernel(K, ls);
+  if (!found) return MT_EUNSUPPORTED;
+  p->graph_bytes = p->gcache ? graph_bytes : 0;
+  p->hist_bytes = hist_bytes;
+  p->lab_bytes = lab_bytes;
+  p->buf_bytes = buf_bytes;
+  const void* kern = pick_kernel(K, p->gcache, p->lab_smem);
   MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)p->smem_bytes));
   int occ = 0;
-  MT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, p->smem_bytes));
+  MT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, p->warps_per_block * 32,
+                                                            p->smem_bytes));
   if (occ < 1) return MT_EUNSUPPORTED;
   p->blocks = sms * occ;
-  const double target = (double)p->blocks * wpb * kTargetItemsPerWarp;
+  const double target = (double)p->blocks * p->warps_per_block * kTargetItemsPerWarp;
   p->items_max = (uint64_t)(target * 1.25) + (uint64_t)G * nmax + 2 * (uint64_t)fwd_bound + 4096;
-  // workspace layout
   size_t off = 0;
   p->off_hdr = off; off += 256;
+  p->off_qhead = off; off += round16((size_t)G * 4);
   p->off_est = off; off += round16((size_t)G * p->entry_stride * 4) * 2;
   p->off_cnt = off; off += round16(((size_t)G * nmax + 1) * 4);
   p->off_items = off; off += round16(p->items_max * sizeof(Item));
   p->off_lab = off;
-  if (!ls) off += round16((size_t)p->blocks * wpb * nmax * 2);
+  if (!p->lab_smem) off += round16((size_t)p->blocks * p->warps_per_block * nmax * (K <= 5 ? 1 : 2));
   p->ws_bytes = off + 256;
   return MT_OK;
 }
@@ -504,12 +594,14 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
                              const uint32_t* table, int32_t rb, int32_t re, cudaStream_t s) {
   char* base = (char*)ws;
   Hdr* hdr = (Hdr*)(base + p.off_hdr);
+  uint32_t* qhead = (uint32_t*)(base + p.off_qhead);
   float* est = (float*)(base + p.off_est);
   int32_t* x1s = (int32_t*)(base + p.off_est + round16((size_t)p.G * p.entry_stride * 4));
   int32_t* cnt = (int32_t*)(base + p.off_cnt);
   Item* items = (Item*)(base + p.off_items);
-  uint16_t* lab = (uint16_t*)(base + p.off_lab);
+  void* lab = base + p.off_lab;
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(Hdr), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(qhead, 0, (size_t)p.G * 4, s);
   if (e != cudaSuccess) return e;
   const int ex = (int)std::min<int64_t>((p.entry_stride + 255) / 256, 4096);
   k_plan_est<K><<<dim3(ex, p.G), 256, 0, s>>>(graphs, p.entry_stride, est, x1s, hdr, rb, re);
@@ -523,20 +615,34 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
                                                       cnt, items, p.items_max, hdr, p.split_cost,
                                                       target, rb, re);
   if (!p.lab_smem) {
-    e = cudaMemsetAsync(lab, 0, (size_t)p.blocks * p.warps_per_block * p.nmax * 2, s);
+    e = cudaMemsetAsync(lab, 0, (size_t)p.blocks * p.warps_per_block * p.nmax * (K <= 5 ? 1 : 2), s);
     if (e != cudaSuccess) return e;
   }
-  const int lab_bytes = (int)round16((size_t)p.nmax * 2);
-  const int buf_bytes = (int)round16((size_t)p.cap * 2);
-  const int hist_bytes = K <= 4 ? (int)round16((size_t)p.classes * 4) : 0;
-  if (p.lab_smem)
-    k_count<K, true><<<p.blocks, p.warps_per_block * 32, p.smem_bytes, s>>>(
-        graphs, items, cnt + (size_t)p.G * p.nmax, p.items_max, hdr, table, lab, p.nmax, p.cap,
-        p.classes, lab_bytes, buf_bytes, hist_bytes);
-  else
-    k_count<K, false><<<p.blocks, p.warps_per_block * 32, p.smem_bytes, s>>>(
-        graphs, items, cnt + (size_t)p.G * p.nmax, p.items_max, hdr, table, lab, p.nmax, p.cap,
-        p.classes, lab_bytes, buf_bytes, hist_bytes);
+  CountArgs a;
+  a.graphs = graphs;
+  a.items = items;
+  a.item_off = cnt;
+  a.qhead = qhead;
+  a.hdr = hdr;
+  a.table = table;
+  a.lab_global = lab;
+  a.G = p.G;
+  a.nmax = p.nmax;
+  a.nu_cap = p.nu_cap;
+  a.cap = p.cap;
+  a.classes = p.classes;
+  a.graph_bytes = (int)p.graph_bytes;
+  a.hist_bytes = (int)p.hist_bytes;
+  a.lab_bytes = (int)p.lab_bytes;
+  a.buf_bytes = (int)p.buf_bytes;
+  const unsigned threads = p.warps_per_block * 32;
+  if (p.gcache) {
+    if (p.lab_smem) k_count<K, true, true><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+    else k_count<K, true, false><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+  } else {
+    if (p.lab_smem) k_count<K, false, true><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+    else k_count<K, false, false><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -19,7 +19,10 @@ struct CountPlan {
   int64_t entry_stride = 0; // per-graph stride of the planner's entry arrays (>= max nu)
   int warps_per_block = 0;
   int blocks = 0;
-  bool lab_smem = true;
+  bool lab_smem = true;      // relation words in shared memory (else global slabs)
+  bool gcache = true;        // the current graph's CSR copied into shared memory
+  int nu_cap = 0;            // capacity of that copy (undirected entries)
+  size_t graph_bytes = 0, hist_bytes = 0, lab_bytes = 0, buf_bytes = 0;
   int cap = 0;              // stack entries per warp
   size_t smem_bytes = 0;
   uint64_t items_max = 0;
@@ -27,7 +30,7 @@ struct CountPlan {
   uint32_t classes = 0;
   size_t ws_bytes = 0;
   // workspace offsets
-  size_t off_hdr = 0, off_est = 0, off_cnt = 0, off_items = 0, off_lab = 0;
+  size_t off_hdr = 0, off_qhead = 0, off_est = 0, off_cnt = 0, off_items = 0, off_lab = 0;
 };
 
 // Fill in the launch shape and the workspace size.  `fwd_bound` is a bound on
