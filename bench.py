@@ -276,6 +276,13 @@ def run_ours(args, world, rank, local):
                     "peak_source": f"152 SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_mhz} MHz "
                                    f"({src} sm_max_mhz)"}
 
+    extra = {}
+    if rank == 0 and not args.no_extra and args.workload == "nullmodel_k5" and args.nulls is None:
+        extra["plain_vs_batched"] = measure_plain_vs_batched(
+            mt, torch, dg, table, g, (1 + R) / (total_ms / args.steps / 1000.0))
+        extra["k6_batch"] = measure_k6(mt, torch)
+        extra["serving"] = measure_serving(mt, torch, {5: table})
+
     if rank == 0:
         line = {"metric": "k-subgraphs classified/s", "value": value, "unit": "subgraphs/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -288,9 +295,119 @@ def run_ours(args, world, rank, local):
                 "table_build_ms": table_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _timed(torch, fn, steps, flush):
+    """Device time (ms) of `steps` calls of fn, L2 flushed before each call."""
+    stream = torch.cuda.current_stream()
+    total = 0.0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total
+
+
+def measure_k6(mt, torch, steps=3, warmup=3):
+    """The k=6 null-model batch: Chung-Lu n=800, m=3,200 plus 64 nulls."""
+    w = syn.WORKLOADS["nullmodel_k6"]
+    g = syn.workload_graph("nullmodel_k6")
+    t0 = time.perf_counter()
+    t = mt.table_build(6)
+    table_ms = 1000 * (time.perf_counter() - t0)
+    dg = mt.graph_from(g)
+    R = w["nulls"]
+    b = mt.Batch(dg, t, R, 10 * g.m)
+    seeds = np.arange(1, R + 1, dtype=np.uint64)
+    hists = torch.empty((R + 1, t.num_classes), dtype=torch.int64, device="cuda")
+    z = torch.empty(t.num_classes, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        b.run(seeds, hists, z)
+    torch.cuda.synchronize()
+    sub = int(mt.to_numpy_u64(hists).sum())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = _timed(torch, lambda: b.run(seeds, hists, z), steps, flush)
+    out = {"value": sub * steps / (ms / 1000.0), "unit": "subgraphs/s",
+           "graphs_per_s": (R + 1) * steps / (ms / 1000.0), "ms_per_step": ms / steps,
+           "subgraphs_per_step": sub, "graphs_per_step": R + 1, "table_build_ms": table_ms,
+           "config": "Chung-Lu n=800 m=3200 gamma 2.5 dmax 40 r 0.10 + 64 nulls, k=6"}
+    b.free()
+    t.free()
+    return out
+
+
+def measure_plain_vs_batched(mt, torch, dg, table, g, batched_graphs_per_s, nplain=16):
+    """One launch per graph (mt_count on the original and `nplain` null graphs
+    made by mt_randomize) against the batched step's graphs/s.  The plain time
+    excludes making the null graphs; the batched time includes it."""
+    graphs = [dg] + [mt.randomize(dg, s, 10 * g.m) for s in range(1, nplain + 1)]
+    out = torch.empty(table.num_classes, dtype=torch.int64, device="cuda")
+    for gr in graphs:
+        mt.count(gr, table, out)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    it = iter(range(10**9))
+    ms = _timed(torch, lambda: mt.count(graphs[next(it) % len(graphs)], table, out),
+                len(graphs), flush)
+    plain = len(graphs) / (ms / 1000.0)
+    return {"plain_graphs_per_s": plain, "batched_graphs_per_s": batched_graphs_per_s,
+            "batched_over_plain": batched_graphs_per_s / plain, "plain_graphs": len(graphs),
+            "note": "plain = one mt_count launch per graph, null graphs made beforehand; "
+                    "batched = randomise + rebuild + count + z in one captured step"}
+
+
+def _work_bound(g, k):
+    from math import comb
+    s, d = g.arcs()
+    deg = np.bincount(s, minlength=g.n) + np.bincount(d, minlength=g.n)
+    return sum(comb(int(x), k - 1) for x in deg)
+
+
+def serving_requests(num, seed):
+    """Seeded request stream; requests whose work bound sum_v C(d_v, k-1)
+    exceeds 2e9 are redrawn."""
+    out, s = [], seed
+    while len(out) < num:
+        for k, g, _ in syn.serving_stream(num, s):
+            if _work_bound(g, k) <= 2e9 and len(out) < num:
+                out.append((k, g))
+        s += 1
+    return out
+
+
+def measure_serving(mt, torch, have_tables, num=32, seed=0):
+    """Continuous-batching server on a seeded stream of mixed-k requests:
+    closed-loop capacity first, then Poisson arrivals at 80% of it."""
+    from paper_1804_09741_gb300.server import Server, poisson_arrivals, run_stream
+    reqs = serving_requests(num, seed)
+    tables = dict(have_tables)
+    for k in (3, 4, 5, 6):
+        if k not in tables:
+            tables[k] = mt.table_build(k)
+    srv = Server(tables, memory_budget=16 << 30, max_slots=32, round_cost=4e8)
+    run_stream(srv, reqs[:4])  # warm-up
+    res, lat, wall = run_stream(srv, reqs)
+    cap = num / wall
+    rate = 0.8 * cap
+    res, lat, wall2 = run_stream(srv, reqs, poisson_arrivals(num, rate, seed + 1))
+    ok = all(r[0] == 2 for r in res)
+    sub = sum(int(r[1].sum()) for r in res if r[1] is not None)
+    srv.free()
+    ks = [k for k, _ in reqs]
+    return {"graphs_per_s": num / wall2, "capacity_graphs_per_s": cap,
+            "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "subgraphs_per_s": sub / wall2,
+            "requests": num, "k_mix": {str(k): ks.count(k) for k in (3, 4, 5, 6)},
+            "n_range": [int(min(g.n for _, g in reqs)), int(max(g.n for _, g in reqs))],
+            "all_ok": ok}
 
 
 # Algorithmic integer operations per classified subgraph in the leaf loop:
@@ -308,6 +425,8 @@ def main():
     ap.add_argument("--workload", default="nullmodel_k5", choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the k=6 batch, plain-vs-batched and serving measurements")
     ap.add_argument("--nulls", type=int, default=None,
                     help="number of null graphs (default: the workload's); smaller values make "
                          "the small cases profiled under ncu, recorded in config")

@@ -69,6 +69,7 @@ typedef enum {
 typedef struct mt_graph mt_graph;
 typedef struct mt_table mt_table;
 typedef struct mt_batch mt_batch;
+typedef struct mt_server mt_server;
 
 /* Text for a status code (static storage). */
 const char* mt_status_str(mt_status s);
@@ -243,6 +244,48 @@ mt_status mt_batch_error(const mt_batch* b, uint32_t* err);
 /* One-shot form of the batch: create, run, free. */
 mt_status mt_count_batch(const mt_graph* g, const mt_table* t, const uint64_t* seeds, int R,
                          uint64_t swaps, uint64_t* hists, double* z, void* stream);
+
+/* ----------------------------------------------------------------- serving */
+
+/* A request server with continuous batching (the paper has no serving layer;
+ * its parallelism is threads over graphs, Sec. 4).  The per-k tables given here
+ * (NULL = that k is not served) stay resident.  Requests are admitted in
+ * arrival order while fewer than `max_slots` are active and their device
+ * memory (graph + histogram + a planner share, counted by the server) fits in
+ * `memory_budget` bytes.  Work runs in rounds: each round gives every active
+ * request a root range whose estimated cost is its share of `round_cost`
+ * (estimated k-subgraphs; a k-set belongs to its smallest vertex, so the
+ * ranges of one request never overlap) and launches one enumeration per k over
+ * all requests' ranges.  A request that arrives while a round runs joins the
+ * next round.  The server owns two CUDA streams; one host thread drives it. */
+mt_status mt_server_create(const mt_table* t3, const mt_table* t4, const mt_table* t5,
+                           const mt_table* t6, size_t memory_budget, int max_slots,
+                           double round_cost, mt_server** out);
+mt_status mt_server_free(mt_server* s);
+
+/* Queue a count request for H_k of the graph given as a HOST CSR (copied; the
+ * caller may free it on return).  Validated like mt_graph_load_csr.  *id
+ * identifies the request.  Errors: MT_EINVAL, MT_EUNSUPPORTED (no table for k
+ * or n > 65535). */
+mt_status mt_server_submit(mt_server* s, int k, int32_t n, int32_t m, const int32_t* row_ptr,
+                           const int32_t* col, uint64_t* id);
+
+/* Run one round: admit what fits, launch this round's work, and complete the
+ * requests whose last range ran in the previous round (waits for that round
+ * only).  Reports how many requests completed, and how many are active and
+ * pending afterwards (any pointer may be NULL). */
+mt_status mt_server_step(mt_server* s, int32_t* completed, int32_t* active, int32_t* pending);
+
+/* State of a request: 0 pending, 1 active, 2 done, 3 failed.  When done and
+ * `hist` (HOST uint64[C]) is given, copies H_k and forgets the request.  A
+ * failed request returns its error (MT_EINVAL for a duplicate arc found on the
+ * device, MT_EBUSY when it can never fit the budget) and is forgotten.
+ * `latency_ms` = completion time - submission time on the host clock. */
+mt_status mt_server_result(mt_server* s, uint64_t id, int32_t* state, uint64_t* hist,
+                           double* latency_ms);
+
+/* Device bytes currently charged against the budget by active requests. */
+mt_status mt_server_used_bytes(const mt_server* s, size_t* used);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,13 @@ SIGNATURES = {
     "mt_batch_phase_ms": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "mt_batch_error": (ctypes.c_int, [_vp, _P(_u32)]),
     "mt_count_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _u64, _vp, _vp, _vp]),
+    "mt_server_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int, _f64,
+                                        _P(_vp)]),
+    "mt_server_free": (ctypes.c_int, [_vp]),
+    "mt_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _vp, _vp, _P(_u64)]),
+    "mt_server_step": (ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i32)]),
+    "mt_server_result": (ctypes.c_int, [_vp, _u64, _P(_i32), _vp, _P(_f64)]),
+    "mt_server_used_bytes": (ctypes.c_int, [_vp, _P(ctypes.c_size_t)]),
 }
 
 

@@ -172,6 +172,8 @@ static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint
     d.n = n;
     d.m = m;
     d.nu = 0;
+    d.root_begin = 0;
+    d.root_end = n;
     d.pad = 0;
     d.row_ptr = g0->row_ptr;
     d.col = b->col_sorted + (size_t)r * m1;

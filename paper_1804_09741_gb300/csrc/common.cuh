@@ -32,6 +32,8 @@ struct DevGraph {
   int32_t n;
   int32_t m;                // arcs
   int32_t nu;               // undirected adjacency entries (2 * undirected edges)
+  int32_t root_begin;       // only k-sets whose smallest vertex is in
+  int32_t root_end;         //   [root_begin, root_end) are counted
   int32_t pad;
   const int32_t* row_ptr;   // n+1, directed out-CSR (sorted rows)
   const int32_t* col;       // m

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_plan_est(const DevGraph* __restrict__ g
     const int u = (int)(G.ucol[e] & kVertexMask);
     float c = 0.f;
     int x1 = 0;
-    if (u > v && v >= root_begin && v < root_end) {
+    if (u > v && v >= root_begin && v < root_end && v >= G.root_begin && v < G.root_end) {
       const int re = G.urow[v + 1];
       const int f = G.urow[v] + G.ufwd[v];
       const int j1 = e - f;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_plan_items(const DevGraph* __restrict__
   if (v >= nmax) return;
   const int64_t slot = (int64_t)g * nmax + v;
   const DevGraph G = graphs[g];
-  if (v >= G.n || v < root_begin || v >= root_end) {
+  if (v >= G.n || v < root_begin || v >= root_end || v < G.root_begin || v >= G.root_end) {
     if (!WRITE) cnt[slot] = 0;
     return;
   }

@@ -148,6 +148,8 @@ DevGraph dev_view(const mt_graph* g, unsigned long long* hist) {
   d.n = g->n;
   d.m = g->m;
   d.nu = g->nu;
+  d.root_begin = 0;
+  d.root_end = g->n;
   d.pad = 0;
   d.row_ptr = g->row_ptr;
   d.col = g->col;
@@ -159,21 +161,30 @@ DevGraph dev_view(const mt_graph* g, unsigned long long* hist) {
   return d;
 }
 
-// Allocate the device arrays of a graph with n vertices and m arcs.
-mt_status graph_alloc(int32_t n, int32_t m, mt_graph** out) {
+size_t graph_device_bytes(int32_t n, int32_t m) {
+  const size_t m1 = (size_t)(m > 0 ? m : 1);
+  const size_t ints = (size_t)(n + 1) + m1 + (size_t)(n + 1) + 2 * m1 + 2 * m1 + (size_t)n;
+  return ints * 4 + 256;
+}
+
+// Allocate the device arrays of a graph with n vertices and m arcs (with
+// cudaMallocAsync on `s` when `pooled`).
+static mt_status graph_alloc_impl(int32_t n, int32_t m, bool pooled, cudaStream_t s,
+                                  mt_graph** out) {
   mt_graph* g = new mt_graph();
   g->n = n;
   g->m = m;
   const size_t m1 = (size_t)(m > 0 ? m : 1);
-  const size_t ints = (size_t)(n + 1) + m1 + (size_t)(n + 1) + 2 * m1 + 2 * m1 + (size_t)n;
   void* mem = nullptr;
-  cudaError_t e = cudaMalloc(&mem, ints * 4 + 256);
+  cudaError_t e = pooled ? cudaMallocAsync(&mem, graph_device_bytes(n, m), s)
+                         : cudaMalloc(&mem, graph_device_bytes(n, m));
   if (e != cudaSuccess) {
     delete g;
     set_last_error(cudaGetErrorString(e));
     return MT_ENOMEM;
   }
   g->mem = mem;
+  g->pooled = pooled;
   int32_t* p = (int32_t*)mem;
   g->row_ptr = p; p += n + 1;
   g->col = p; p += m1;
@@ -183,6 +194,69 @@ mt_status graph_alloc(int32_t n, int32_t m, mt_graph** out) {
   g->ufwd = p; p += n;
   *out = g;
   return MT_OK;
+}
+
+mt_status graph_alloc(int32_t n, int32_t m, mt_graph** out) {
+  return graph_alloc_impl(n, m, false, nullptr, out);
+}
+
+void graph_release(mt_graph* g, cudaStream_t s) {
+  if (!g) return;
+  if (g->pooled) {
+    if (g->mem) cudaFreeAsync(g->mem, s);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+  } else {
+    mt_graph_free(g);
+  }
+}
+
+mt_status validate_csr(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col) {
+  if (!row_ptr || (m > 0 && !col) || n < 1 || m < 0) return MT_EINVAL;
+  if (n > kMaxVertices) return MT_EUNSUPPORTED;
+  if (row_ptr[0] != 0 || row_ptr[n] != m) return MT_EINVAL;
+  for (int32_t v = 0; v < n; ++v) {
+    if (row_ptr[v + 1] < row_ptr[v]) return MT_EINVAL;
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+      if (col[e] < 0 || col[e] >= n || col[e] == v) return MT_EINVAL;
+  }
+  return MT_OK;
+}
+
+mt_status graph_build_sync(mt_graph* g, const int32_t* col_in, cudaStream_t s);
+
+static mt_status graph_load_impl(int32_t n, int32_t m, const int32_t* row_ptr,
+                                 const int32_t* col, bool pooled, cudaStream_t s,
+                                 mt_graph** out) {
+  MT_TRY(validate_csr(n, m, row_ptr, col));
+  mt_graph* g = nullptr;
+  MT_TRY(graph_alloc_impl(n, m, pooled, s, &g));
+  int32_t* col_in = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&col_in, (size_t)(m > 0 ? m : 1) * 4, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->row_ptr, row_ptr, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && m > 0)
+    e = cudaMemcpyAsync(col_in, col, (size_t)m * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    if (col_in) cudaFreeAsync(col_in, s);
+    graph_release(g, s);
+    return MT_ECUDA;
+  }
+  mt_status st = graph_build_sync(g, col_in, s);
+  cudaFreeAsync(col_in, s);
+  if (st != MT_OK) {
+    graph_release(g, s);
+    return st;
+  }
+  *out = g;
+  return MT_OK;
+}
+
+mt_status graph_load_on(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col,
+                        cudaStream_t s, mt_graph** out) {
+  return graph_load_impl(n, m, row_ptr, col, true, s, out);
 }
 
 // Build the sorted and undirected CSRs of `g` from unsorted destinations
@@ -243,37 +317,8 @@ const char* mt_last_error(void) { return g_last_error.c_str(); }
 
 mt_status mt_graph_load_csr(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col,
                             void* stream, mt_graph** out) {
-  if (!out || !row_ptr || (m > 0 && !col) || n < 1 || m < 0) return MT_EINVAL;
-  if (n > kMaxVertices) return MT_EUNSUPPORTED;
-  if (row_ptr[0] != 0 || row_ptr[n] != m) return MT_EINVAL;
-  for (int32_t v = 0; v < n; ++v) {
-    if (row_ptr[v + 1] < row_ptr[v]) return MT_EINVAL;
-    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
-      if (col[e] < 0 || col[e] >= n || col[e] == v) return MT_EINVAL;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  mt_graph* g = nullptr;
-  MT_TRY(graph_alloc(n, m, &g));
-  int32_t* col_in = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&col_in, (size_t)(m > 0 ? m : 1) * 4, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(g->row_ptr, row_ptr, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && m > 0)
-    e = cudaMemcpyAsync(col_in, col, (size_t)m * 4, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
-    set_last_error(cudaGetErrorString(e));
-    if (col_in) cudaFreeAsync(col_in, s);
-    mt_graph_free(g);
-    return MT_ECUDA;
-  }
-  mt_status st = graph_build_sync(g, col_in, s);
-  cudaFreeAsync(col_in, s);
-  if (st != MT_OK) {
-    mt_graph_free(g);
-    return st;
-  }
-  *out = g;
-  return MT_OK;
+  if (!out) return MT_EINVAL;
+  return graph_load_impl(n, m, row_ptr, col, false, (cudaStream_t)stream, out);
 }
 
 mt_status mt_graph_free(mt_graph* g) {

@@ -14,6 +14,7 @@ struct mt_graph {
   int32_t* usrc = nullptr;     // device, 2m
   int32_t* ufwd = nullptr;     // device, n
   void* mem = nullptr;         // one allocation backing all of the above
+  bool pooled = false;         // mem came from the stream-ordered pool (cudaMallocAsync)
 
   // Counting scratch, grown on demand by mt_count.
   void* ws = nullptr;
@@ -61,5 +62,15 @@ inline size_t build_scratch_ints(int32_t n, int32_t m) {
 }
 
 DevGraph dev_view(const mt_graph* g, unsigned long long* hist);
+
+// Host-side checks of a CSR (MT_OK, MT_EINVAL or MT_EUNSUPPORTED).
+mt_status validate_csr(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col);
+
+// Load a graph with stream-ordered allocations on `s` (no device-wide sync);
+// release it with graph_release on a stream.  Synchronises `s` only.
+mt_status graph_load_on(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col,
+                        cudaStream_t s, mt_graph** out);
+void graph_release(mt_graph* g, cudaStream_t s);
+size_t graph_device_bytes(int32_t n, int32_t m);
 
 }  // namespace mt

@@ -1,0 +1,125 @@
+"""The continuous-batching server: every result equals the same graph counted
+alone (bit-exact), requests arriving mid-flight overtake a long one, memory
+budget and slots bound admission, bad requests fail alone.  GPU only."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tables():
+    import paper_1804_09741_gb300 as mt
+    mt.load_library()
+    return {k: mt.table_build(k) for k in (3, 4, 5, 6)}
+
+
+def alone(mt, t, g):
+    return mt.count_host(mt.graph_from(g), t)
+
+
+def test_mixed_stream_equals_alone(tables):
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server, poisson_arrivals, run_stream
+    reqs = []
+    rng = np.random.default_rng(3)
+    for i in range(24):
+        k = [3, 4, 5, 6][i % 4]
+        n = int(rng.integers(30, 900 if k < 6 else 300))
+        g = syn.chung_lu_digraph(n, int(n * rng.uniform(2, 4)), 2.3, 30, 0.2, 1000 + i)
+        reqs.append((k, g))
+    reqs += [(4, syn.empty_graph(7)), (5, syn.empty_graph(1)), (6, syn.complete_digraph(5)),
+             (3, syn.complete_digraph(9))]
+    srv = Server(tables, memory_budget=2 << 30, max_slots=8, round_cost=2e6)
+    out, lat, wall = run_stream(srv, reqs, poisson_arrivals(len(reqs), 400.0, 1))
+    for (k, g), (st, hist, status) in zip(reqs, out):
+        assert st == 2, status
+        np.testing.assert_array_equal(hist, alone(mt, tables[k], g))
+    assert np.all(lat > 0)
+    assert srv.used_bytes() == 0
+    srv.free()
+
+
+def test_late_small_requests_overtake_a_long_one(tables):
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server
+    big = syn.workload_graph("nullmodel_k5")
+    srv = Server(tables, memory_budget=4 << 30, max_slots=16, round_cost=2e7)
+    bid = srv.submit(5, big)
+    for _ in range(3):
+        srv.step()
+    small = [syn.chung_lu_digraph(200, 600, 2.3, 20, 0.1, 50 + i) for i in range(4)]
+    sids = [srv.submit(4, g) for g in small]
+    done_small, big_done_at, step = {}, None, 0
+    results = {}
+    while big_done_at is None or len(done_small) < 4:
+        srv.step()
+        step += 1
+        for sid, g in zip(sids, small):
+            if sid not in done_small:
+                st, h, ms, _ = srv.result(sid, 4)
+                if st == 2:
+                    done_small[sid] = step
+                    results[sid] = h
+        if big_done_at is None:
+            st, h, ms, _ = srv.result(bid, 5)
+            if st == 2:
+                big_done_at = step
+                big_hist = h
+        assert step < 100000
+    assert max(done_small.values()) < big_done_at  # admitted mid-flight, finished first
+    np.testing.assert_array_equal(big_hist, alone(mt, tables[5], big))
+    for sid, g in zip(sids, small):
+        np.testing.assert_array_equal(results[sid], alone(mt, tables[4], g))
+    srv.free()
+
+
+def test_budget_and_slots_bound_admission(tables):
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server, run_stream
+    graphs = [syn.chung_lu_digraph(800, 3000, 2.4, 40, 0.1, 70 + i) for i in range(6)]
+    # room for about two requests at a time
+    per = 4 * (3 * 801 + 5 * 3000) + 64 * 3800 + 13 * 8 + 8192
+    srv = Server(tables, memory_budget=2 * per + 1000, max_slots=3, round_cost=1e6)
+    ids = [srv.submit(3, g) for g in graphs]
+    seen_pending, max_active = False, 0
+    remaining = set(ids)
+    res = {}
+    while remaining:
+        c, a, p = srv.step()
+        max_active = max(max_active, a)
+        seen_pending |= p > 0
+        assert srv.used_bytes() <= 2 * per + 1000
+        for rid in list(remaining):
+            st, h, ms, _ = srv.result(rid, 3)
+            if st == 2:
+                res[rid] = h
+                remaining.discard(rid)
+    assert seen_pending and max_active <= 2
+    for rid, g in zip(ids, graphs):
+        np.testing.assert_array_equal(res[rid], alone(mt, tables[3], g))
+    # a request that can never fit the budget fails on its own
+    bid = srv.submit(6, syn.workload_graph("nullmodel_k6"))
+    for _ in range(3):
+        srv.step()
+    st, h, ms, status = srv.result(bid, 6)
+    assert st == 3 and status == mt.MT_EBUSY
+    srv.free()
+
+
+def test_bad_request_fails_alone(tables):
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server, run_stream
+    dup = syn.Graph(3, np.array([0, 2, 2, 2], np.int32), np.array([1, 1], np.int32))
+    good = syn.chung_lu_digraph(300, 900, 2.3, 30, 0.1, 5)
+    srv = Server(tables, round_cost=1e6)
+    out, lat, wall = run_stream(srv, [(4, good), (4, dup), (4, good)])
+    assert out[1][0] == 3 and out[1][2] == mt.MT_EINVAL
+    for i in (0, 2):
+        assert out[i][0] == 2
+        np.testing.assert_array_equal(out[i][1], alone(mt, tables[4], good))
+    with pytest.raises(mt.MotifsError):
+        srv.submit(4, syn.Graph(2, np.array([0, 1, 1], np.int32), np.array([0], np.int32)))
+    srv.free()
