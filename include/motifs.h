@@ -162,13 +162,29 @@ mt_status mt_count(const mt_graph* g, const mt_table* t, uint64_t* hist, void* s
 mt_status mt_count_roots(const mt_graph* g, const mt_table* t, int32_t root_begin,
                          int32_t root_end, uint64_t* hist, void* stream);
 
-/* Same as mt_count with explicit tuning: `split_cost` is the estimated work
- * (in classified subgraphs) above which a first-level extension branch is
- * split into second-level work items, and the size of first-level items
- * (0 = automatic: the total estimate spread over 24 items per resident warp);
- * `warps_per_block` is the block size in warps (0 = automatic, else 1..32). */
-mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist, double split_cost,
-                         int warps_per_block, void* stream);
+/* Launch tuning of the enumerator (all fields 0 = automatic).
+ * - split_cost: estimated work (classified subgraphs) above which a first-level
+ *   extension branch of a root is split into second-level work items, and the
+ *   target size of first-level items; the root-split threshold.
+ * - split_scale: when split_cost is 0, a multiplier of the automatic threshold
+ *   (the graph's total estimate spread over 24 items per resident warp).
+ *   The threshold is never set below 1/5 of the automatic one, which bounds the
+ *   number of work items.
+ * - warps_per_block: block size in warps, 1..32.
+ * - stack_cap: candidate-stack entries per warp (the stack depth).  Automatic is
+ *   (k-1) * max degree + 32, which cannot overflow; a smaller value saves shared
+ *   memory, and an overflow is detected and reported as MT_EOVERFLOW. */
+typedef struct {
+  double split_cost;
+  double split_scale;
+  int warps_per_block;
+  int stack_cap;
+} mt_tuning;
+
+/* mt_count with explicit tuning (`tuning` may be NULL = automatic).
+ * Errors as mt_count, plus MT_EINVAL for out-of-range fields. */
+mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
+                         const mt_tuning* tuning, void* stream);
 
 /* mt_count for programs that must not allocate GPU memory while they run: a
  * service that reserves its whole device-memory budget at start-up (its own
@@ -222,6 +238,10 @@ mt_status mt_randomize(const mt_graph* src, uint64_t seed, uint64_t swaps, void*
 mt_status mt_batch_create(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
                           mt_batch** out);
 mt_status mt_batch_free(mt_batch* b);
+
+/* mt_batch_create with explicit tuning of the counting launch (NULL = automatic). */
+mt_status mt_batch_create_tuned(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
+                                const mt_tuning* tuning, mt_batch** out);
 
 /* Run a batch.  `seeds`: HOST array of R uint64.  `hists`: uint64[(R+1)*C]
  * (row 0 = original graph, row r = null graph r), device or host.  `z`:

@@ -28,6 +28,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmotifs.so")
 MT_OK, MT_EINVAL, MT_EUNSUPPORTED, MT_ENOMEM, MT_ECUDA, MT_ETIMEOUT, MT_EOVERFLOW, MT_EBUSY = range(8)
 NUM_CLASSES = {3: 13, 4: 199, 5: 9364, 6: 1530843}
 
+class Tuning(ctypes.Structure):
+    """mt_tuning: root-split threshold (absolute or scale of the automatic one),
+    block size in warps, candidate-stack entries per warp; 0 = automatic."""
+    _fields_ = [("split_cost", ctypes.c_double), ("split_scale", ctypes.c_double),
+                ("warps_per_block", ctypes.c_int), ("stack_cap", ctypes.c_int)]
+
+
 # Every entry point of include/motifs.h with its ctypes signature.
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
@@ -47,11 +54,12 @@ SIGNATURES = {
     "mt_table_entries": (ctypes.c_int, [_vp, _u64, _u64, _vp]),
     "mt_count": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_count_roots": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
-    "mt_count_tuned": (ctypes.c_int, [_vp, _vp, _vp, _f64, ctypes.c_int, _vp]),
+    "mt_count_tuned": (ctypes.c_int, [_vp, _vp, _vp, _P(Tuning), _vp]),
     "mt_count_stats": (ctypes.c_int, [_vp, _P(_u64), _P(_u32), _P(ctypes.c_float)]),
     "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_randomize": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_batch_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(_vp)]),
+    "mt_batch_create_tuned": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(Tuning), _P(_vp)]),
     "mt_batch_free": (ctypes.c_int, [_vp]),
     "mt_batch_run": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "mt_batch_phase_ms": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
@@ -246,11 +254,17 @@ def count_roots(g: Graph, t: Table, root_begin: int, root_end: int, stream=None)
     return out
 
 
+def make_tuning(split_cost: float = 0.0, warps_per_block: int = 0, split_scale: float = 0.0,
+                stack_cap: int = 0) -> Tuning:
+    return Tuning(float(split_cost), float(split_scale), int(warps_per_block), int(stack_cap))
+
+
 def count_tuned(g: Graph, t: Table, split_cost: float = 0.0, warps_per_block: int = 0, out=None,
-                stream=None):
+                stream=None, split_scale: float = 0.0, stack_cap: int = 0):
     out = _dev_hist(t, out)
-    _check(_lib.mt_count_tuned(g.handle, t.handle, out.data_ptr(), float(split_cost),
-                               int(warps_per_block), _stream(stream)), "mt_count_tuned")
+    tun = make_tuning(split_cost, warps_per_block, split_scale, stack_cap)
+    _check(_lib.mt_count_tuned(g.handle, t.handle, out.data_ptr(), ctypes.byref(tun),
+                               _stream(stream)), "mt_count_tuned")
     return out
 
 
@@ -294,11 +308,15 @@ def randomize(g: Graph, seed: int, swaps: int, stream=None) -> Graph:
 class Batch:
     """The original graph plus R null graphs counted in one captured step."""
 
-    def __init__(self, g: Graph, t: Table, R: int, swaps: int):
+    def __init__(self, g: Graph, t: Table, R: int, swaps: int, tuning: Tuning | None = None):
         self.g, self.t, self.R, self.swaps = g, t, R, swaps
         h = _vp()
-        _check(_lib.mt_batch_create(g.handle, t.handle, R, swaps, ctypes.byref(h)),
-               "mt_batch_create")
+        if tuning is None:
+            _check(_lib.mt_batch_create(g.handle, t.handle, R, swaps, ctypes.byref(h)),
+                   "mt_batch_create")
+        else:
+            _check(_lib.mt_batch_create_tuned(g.handle, t.handle, R, swaps, ctypes.byref(tuning),
+                                              ctypes.byref(h)), "mt_batch_create_tuned")
         self.handle = h.value
 
     def run(self, seeds, hists=None, z=None, stream=None):

@@ -86,7 +86,7 @@ __global__ void k_zscore(const unsigned long long* hists, int R, uint32_t C, dou
 static size_t r16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint64_t swaps,
-                              mt_batch** out) {
+                              const mt_tuning* tuning, mt_batch** out) {
   const int K = table_k(t);
   const uint32_t C = table_classes(t);
   const int32_t n = g0->n, m = g0->m;
@@ -102,8 +102,9 @@ static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint
 
   mt_batch* b = new mt_batch();
   b->g0 = g0; b->t = t; b->R = R; b->swaps = swaps; b->K = K; b->C = C; b->n = n; b->m = m;
-  mt_status st = count_configure(&b->plan, K, R + 1, n, dbound, (int64_t)(R + 1) * std::max(m, 1),
-                                 2 * (int64_t)std::max(m, 1), C, 0.0, 0);
+  mt_status st = count_configure_tuned(&b->plan, K, R + 1, n, dbound,
+                                       (int64_t)(R + 1) * std::max(m, 1),
+                                       2 * (int64_t)std::max(m, 1), C, tuning);
   if (st != MT_OK) {
     delete b;
     return st;
@@ -279,7 +280,17 @@ extern "C" {
 mt_status mt_batch_create(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
                           mt_batch** out) {
   if (!g || !t || !out || R < 1) return MT_EINVAL;
-  return batch_create(g, t, R, swaps, out);
+  return batch_create(g, t, R, swaps, nullptr, out);
+}
+
+mt_status mt_batch_create_tuned(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
+                                const mt_tuning* tuning, mt_batch** out) {
+  if (!g || !t || !out || R < 1) return MT_EINVAL;
+  if (tuning && (tuning->split_cost < 0 || tuning->split_scale < 0 ||
+                 tuning->warps_per_block < 0 || tuning->warps_per_block > 32 ||
+                 tuning->stack_cap < 0 || tuning->stack_cap > 65535))
+    return MT_EINVAL;
+  return batch_create(g, t, R, swaps, tuning, out);
 }
 
 mt_status mt_batch_free(mt_batch* b) {

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(256) k_plan_items(const DevGraph* __restrict__
                                                     int64_t stride, const float* est,
                                                     const int32_t* x1s, int nmax, int32_t* cnt,
                                                     Item* items, uint64_t items_max, Hdr* hdr,
-                                                    double split_cost, double target_items,
+                                                    double split_cost, double split_scale,
+                                                    double target_items, double items_factor,
                                                     int root_begin, int root_end) {
   const int g = blockIdx.y;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,8 +142,12 @@ __global__ void __launch_bounds__(256) k_plan_items(const DevGraph* __restrict__
     if (!WRITE) cnt[slot] = 0;
     return;
   }
-  double T = hdr->total_est / target_items;
-  if (split_cost > T) T = split_cost;
+  // root-split threshold: explicit, or the automatic one scaled; never so small
+  // that the items exceed their budget
+  const double t_auto = hdr->total_est / target_items;
+  double T = split_cost > 0.0 ? split_cost : t_auto * split_scale;
+  const double t_min = hdr->total_est / (items_factor * target_items);
+  if (T < t_min) T = t_min;
   if (T < 1.0) T = 1.0;
   const float Tf = (float)T;
   const int re = G.urow[v + 1];
@@ -386,7 +391,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           const int u = (int)(ent & kVertexMask);
           lab[u] |= (LabT<K>)(ent >> 30);
           const int q = i - f - j1a;
-          if (q >= 0) buf[q] = (uint16_t)u;
+          if (q >= 0) {
+            if (q < w.cap) buf[q] = (uint16_t)u;
+            else atomicOr(w.err, kErrStackOverflow);
+          }
         }
       }
       __syncwarp();
@@ -394,8 +402,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       uint32_t s_key = 0;
       if (lane == 1) {
         s_c = 0;
-        s_ce = j1b - j1a;
-        s_e = dplus - j1a;
+        s_e = min(dplus - j1a, w.cap);
+        s_ce = min(j1b - j1a, s_e);
       }
       if (lane == 0) s_vert = v;
       const bool has2 = it.b2 != 0xFFFF;
@@ -510,7 +518,22 @@ static const void* pick_kernel(int K, bool gc, bool ls) {
 mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
                           int64_t entry_stride, uint32_t classes, double split_cost,
                           int warps_per_block) {
+  mt_tuning t;
+  t.split_cost = split_cost;
+  t.split_scale = 0.0;
+  t.warps_per_block = warps_per_block;
+  t.stack_cap = 0;
+  const bool plain = split_cost == 0.0;
+  MT_TRY(count_configure_tuned(p, K, G, nmax, dmax, fwd_bound, entry_stride, classes,
+                               plain && warps_per_block == 0 ? nullptr : &t));
+  return MT_OK;
+}
+
+mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
+                                int64_t entry_stride, uint32_t classes, const mt_tuning* tuning) {
   if (K < 3 || K > 6 || G < 1 || nmax < 1) return MT_EINVAL;
+  const double split_cost = tuning ? tuning->split_cost : 0.0;
+  const int warps_per_block = tuning ? tuning->warps_per_block : 0;
   p->K = K;
   p->G = G;
   p->nmax = nmax;
@@ -519,7 +542,9 @@ mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_
   p->entry_stride = entry_stride > 0 ? entry_stride : 1;
   p->classes = classes;
   p->split_cost = split_cost;
-  p->cap = (K - 1) * std::max(dmax, 1) + 32;
+  p->split_scale = (tuning && tuning->split_scale > 0.0) ? tuning->split_scale : 1.0;
+  p->items_factor = tuning ? 5.0 : 1.25;
+  p->cap = (tuning && tuning->stack_cap > 0) ? tuning->stack_cap : (K - 1) * std::max(dmax, 1) + 32;
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
   const size_t lab_bytes = round16((size_t)nmax * (K <= 5 ? 1 : 2));
@@ -569,7 +594,8 @@ mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_
   if (occ < 1) return MT_EUNSUPPORTED;
   p->blocks = sms * occ;
   const double target = (double)p->blocks * p->warps_per_block * kTargetItemsPerWarp;
-  p->items_max = (uint64_t)(target * 1.25) + (uint64_t)G * nmax + 2 * (uint64_t)fwd_bound + 4096;
+  p->items_max = (uint64_t)(target * p->items_factor) + (uint64_t)G * nmax +
+                 2 * (uint64_t)fwd_bound + 4096;
   size_t off = 0;
   p->off_hdr = off; off += 256;
   p->off_qhead = off; off += round16((size_t)G * 4);
@@ -609,11 +635,13 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
   const double target = (double)p.blocks * p.warps_per_block * kTargetItemsPerWarp;
   k_plan_items<K, false><<<dim3(rx, p.G), 256, 0, s>>>(graphs, p.entry_stride, est, x1s, p.nmax,
                                                        cnt, items, p.items_max, hdr, p.split_cost,
-                                                       target, rb, re);
+                                                       p.split_scale, target, p.items_factor, rb,
+                                                       re);
   k_scan_counts<<<1, 1024, 0, s>>>(cnt, p.G * p.nmax + 1);
   k_plan_items<K, true><<<dim3(rx, p.G), 256, 0, s>>>(graphs, p.entry_stride, est, x1s, p.nmax,
                                                       cnt, items, p.items_max, hdr, p.split_cost,
-                                                      target, rb, re);
+                                                      p.split_scale, target, p.items_factor, rb,
+                                                      re);
   if (!p.lab_smem) {
     e = cudaMemsetAsync(lab, 0, (size_t)p.blocks * p.warps_per_block * p.nmax * (K <= 5 ? 1 : 2), s);
     if (e != cudaSuccess) return e;
@@ -665,13 +693,13 @@ mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
 
 // Plain one-graph count with the workspace cached in the graph handle.
 static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist,
-                           int32_t rb, int32_t re, double split_cost, int wpb, cudaStream_t s) {
+                           int32_t rb, int32_t re, const mt_tuning* tuning, cudaStream_t s) {
   mt_graph* g = const_cast<mt_graph*>(gc);
   const int K = table_k(t);
   const uint32_t C = table_classes(t);
   CountPlan p;
-  MT_TRY(count_configure(&p, K, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1), C,
-                         split_cost, wpb));
+  MT_TRY(count_configure_tuned(&p, K, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1), C,
+                               tuning));
   // workspace: plan scratch + the DevGraph + a device histogram
   const size_t extra = 256 + round16((size_t)C * 8);
   const size_t need = p.ws_bytes + extra;
@@ -734,19 +762,22 @@ mt_status mt_count_roots(const mt_graph* g, const mt_table* t, int32_t root_begi
   if (!g || !t || !hist) return MT_EINVAL;
   if (root_begin < 0) root_begin = 0;
   if (root_end > g->n) root_end = g->n;
-  return count_one(g, t, hist, root_begin, root_end, 0.0, 0, (cudaStream_t)stream);
+  return count_one(g, t, hist, root_begin, root_end, nullptr, (cudaStream_t)stream);
 }
 
 mt_status mt_count(const mt_graph* g, const mt_table* t, uint64_t* hist, void* stream) {
   if (!g || !t || !hist) return MT_EINVAL;
-  return count_one(g, t, hist, 0, g->n, 0.0, 0, (cudaStream_t)stream);
+  return count_one(g, t, hist, 0, g->n, nullptr, (cudaStream_t)stream);
 }
 
-mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist, double split_cost,
-                         int warps_per_block, void* stream) {
-  if (!g || !t || !hist || split_cost < 0 || warps_per_block < 0 || warps_per_block > 32)
+mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
+                         const mt_tuning* tuning, void* stream) {
+  if (!g || !t || !hist) return MT_EINVAL;
+  if (tuning && (tuning->split_cost < 0 || tuning->split_scale < 0 ||
+                 tuning->warps_per_block < 0 || tuning->warps_per_block > 32 ||
+                 tuning->stack_cap < 0 || tuning->stack_cap > 65535))
     return MT_EINVAL;
-  return count_one(g, t, hist, 0, g->n, split_cost, warps_per_block, (cudaStream_t)stream);
+  return count_one(g, t, hist, 0, g->n, tuning, (cudaStream_t)stream);
 }
 
 mt_status mt_count_stats(const mt_graph* g, uint64_t* items, uint32_t* err, float* ms) {

@@ -27,6 +27,8 @@ struct CountPlan {
   size_t smem_bytes = 0;
   uint64_t items_max = 0;
   double split_cost = 0.0;  // 0 = automatic
+  double split_scale = 1.0; // multiplier of the automatic threshold
+  double items_factor = 1.25;  // work items budget, in units of the automatic target
   uint32_t classes = 0;
   size_t ws_bytes = 0;
   // workspace offsets
@@ -38,6 +40,10 @@ struct CountPlan {
 mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
                           int64_t entry_stride, uint32_t classes, double split_cost,
                           int warps_per_block);
+
+// Same, with the tuning of include/motifs.h (nullptr = automatic).
+mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
+                                int64_t entry_stride, uint32_t classes, const mt_tuning* tuning);
 
 // Enqueue planner + enumerator.  `graphs` is a device array of G DevGraph whose
 // hist pointers are already zeroed (the launch adds into them).  Roots in
