@@ -281,6 +281,11 @@ def run_ours(args, world, rank, local):
         extra["plain_vs_batched"] = measure_plain_vs_batched(
             mt, torch, dg, table, g, (1 + R) / (total_ms / args.steps / 1000.0))
         extra["k6_batch"] = measure_k6(mt, torch)
+        extra["cells_method"] = {
+            "k5_batch": measure_batch_method(mt, torch, "nullmodel_k5", table),
+            "k6_batch": measure_batch_method(mt, torch, "nullmodel_k6", None),
+            "note": "same workloads counted with MT_METHOD_CELLS (Algorithm 1 of Sec. 3: the "
+                    "last two vertices counted per cell pair); histograms identical"}
         extra["serving"] = measure_serving(mt, torch, {5: table})
 
     if rank == 0:
@@ -341,6 +346,42 @@ def measure_k6(mt, torch, steps=3, warmup=3):
            "config": "Chung-Lu n=800 m=3200 gamma 2.5 dmax 40 r 0.10 + 64 nulls, k=6"}
     b.free()
     t.free()
+    return out
+
+
+def measure_batch_method(mt, torch, name, table, method=1, steps=3, warmup=3):
+    """A null-model batch counted with another counting method."""
+    w = syn.WORKLOADS[name]
+    g = syn.workload_graph(name)
+    own = table is None
+    t = mt.table_build(w["k"]) if own else table
+    dg = mt.graph_from(g)
+    R = w["nulls"]
+    b = mt.Batch(dg, t, R, 10 * g.m, mt.make_tuning(method=method))
+    seeds = np.arange(1, R + 1, dtype=np.uint64)
+    hists = torch.empty((R + 1, t.num_classes), dtype=torch.int64, device="cuda")
+    z = torch.empty(t.num_classes, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        b.run(seeds, hists, z)
+    torch.cuda.synchronize()
+    assert b.error() == 0
+    sub = int(mt.to_numpy_u64(hists).sum())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    count_ms = []
+
+    def one():
+        b.run(seeds, hists, z)
+    ms = 0.0
+    for i in range(steps):
+        ms += _timed(torch, one, 1, flush)
+        count_ms.append(b.phase_ms()[1])
+    out = {"metric": "k-subgraphs counted/s", "value": sub * steps / (ms / 1000.0),
+           "unit": "subgraphs/s", "graphs_per_s": (R + 1) * steps / (ms / 1000.0),
+           "ms_per_step": ms / steps, "count_kernel_ms": statistics.mean(count_ms),
+           "subgraphs_per_step": sub}
+    b.free()
+    if own:
+        t.free()
     return out
 
 

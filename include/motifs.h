@@ -162,23 +162,36 @@ mt_status mt_count(const mt_graph* g, const mt_table* t, uint64_t* hist, void* s
 mt_status mt_count_roots(const mt_graph* g, const mt_table* t, int32_t root_begin,
                          int32_t root_end, uint64_t* hist, void* stream);
 
+/* Counting method.
+ * MT_METHOD_ENUMERATE (default): every connected k-set is produced and its class
+ *   read from the table (per-subgraph classification, Sec. 3.2).
+ * MT_METHOD_CELLS: the enumeration stops at (k-2)-sets X; the k-sets X + {y, z}
+ *   are counted per pair of cells of Part(adj(X)) (Sec. 2) with one table read
+ *   per cell pair, arcs between the two added vertices corrected one by one,
+ *   as Algorithm 1 of Sec. 3 does.  Same histogram, far fewer table reads.
+ *   Each k-set is still counted once (the enumerator owns every (k-2)-set once
+ *   and partitions the pairs above it). */
+typedef enum { MT_METHOD_ENUMERATE = 0, MT_METHOD_CELLS = 1 } mt_method;
+
 /* Launch tuning of the enumerator (all fields 0 = automatic).
  * - split_cost: estimated work (classified subgraphs) above which a first-level
  *   extension branch of a root is split into second-level work items, and the
  *   target size of first-level items; the root-split threshold.
  * - split_scale: when split_cost is 0, a multiplier of the automatic threshold
- *   (the graph's total estimate spread over 24 items per resident warp).
+ *   (the graph's total estimate spread over 64 items per resident warp).
  *   The threshold is never set below 1/5 of the automatic one, which bounds the
  *   number of work items.
  * - warps_per_block: block size in warps, 1..32.
  * - stack_cap: candidate-stack entries per warp (the stack depth).  Automatic is
  *   (k-1) * max degree + 32, which cannot overflow; a smaller value saves shared
- *   memory, and an overflow is detected and reported as MT_EOVERFLOW. */
+ *   memory, and an overflow is detected and reported as MT_EOVERFLOW.
+ * - method: an mt_method. */
 typedef struct {
   double split_cost;
   double split_scale;
   int warps_per_block;
   int stack_cap;
+  int method;  /* mt_method */
 } mt_tuning;
 
 /* mt_count with explicit tuning (`tuning` may be NULL = automatic).

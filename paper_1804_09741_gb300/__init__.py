@@ -32,7 +32,11 @@ class Tuning(ctypes.Structure):
     """mt_tuning: root-split threshold (absolute or scale of the automatic one),
     block size in warps, candidate-stack entries per warp; 0 = automatic."""
     _fields_ = [("split_cost", ctypes.c_double), ("split_scale", ctypes.c_double),
-                ("warps_per_block", ctypes.c_int), ("stack_cap", ctypes.c_int)]
+                ("warps_per_block", ctypes.c_int), ("stack_cap", ctypes.c_int),
+                ("method", ctypes.c_int)]
+
+
+METHOD_ENUMERATE, METHOD_CELLS = 0, 1
 
 
 # Every entry point of include/motifs.h with its ctypes signature.
@@ -255,14 +259,18 @@ def count_roots(g: Graph, t: Table, root_begin: int, root_end: int, stream=None)
 
 
 def make_tuning(split_cost: float = 0.0, warps_per_block: int = 0, split_scale: float = 0.0,
-                stack_cap: int = 0) -> Tuning:
-    return Tuning(float(split_cost), float(split_scale), int(warps_per_block), int(stack_cap))
+                stack_cap: int = 0, method: int = METHOD_ENUMERATE) -> Tuning:
+    return Tuning(float(split_cost), float(split_scale), int(warps_per_block), int(stack_cap),
+                  int(method))
 
 
 def count_tuned(g: Graph, t: Table, split_cost: float = 0.0, warps_per_block: int = 0, out=None,
-                stream=None, split_scale: float = 0.0, stack_cap: int = 0):
+                stream=None, split_scale: float = 0.0, stack_cap: int = 0,
+                method: int = METHOD_ENUMERATE):
+    """mt_count_tuned: `method` METHOD_ENUMERATE classifies every k-set,
+    METHOD_CELLS counts the last two vertices per cell pair (Algorithm 1)."""
     out = _dev_hist(t, out)
-    tun = make_tuning(split_cost, warps_per_block, split_scale, stack_cap)
+    tun = make_tuning(split_cost, warps_per_block, split_scale, stack_cap, method)
     _check(_lib.mt_count_tuned(g.handle, t.handle, out.data_ptr(), ctypes.byref(tun),
                                _stream(stream)), "mt_count_tuned")
     return out

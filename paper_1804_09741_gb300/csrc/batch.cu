@@ -288,7 +288,8 @@ mt_status mt_batch_create_tuned(const mt_graph* g, const mt_table* t, int R, uin
   if (!g || !t || !out || R < 1) return MT_EINVAL;
   if (tuning && (tuning->split_cost < 0 || tuning->split_scale < 0 ||
                  tuning->warps_per_block < 0 || tuning->warps_per_block > 32 ||
-                 tuning->stack_cap < 0 || tuning->stack_cap > 65535))
+                 tuning->stack_cap < 0 || tuning->stack_cap > 65535 ||
+                 tuning->method < 0 || tuning->method > 1))
     return MT_EINVAL;
   return batch_create(g, t, R, swaps, tuning, out);
 }

@@ -44,7 +44,7 @@ struct Hdr {
 };
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kTargetItemsPerWarp = 24;
+constexpr int kTargetItemsPerWarp = 64;
 constexpr int kMaxWarpsPerBlock = 32;
 
 __device__ __forceinline__ float choose_f(int x, int r) {
@@ -293,14 +293,19 @@ struct CountArgs {
   void* lab_global;
   int G, nmax, nu_cap, cap;
   uint32_t classes;
-  int graph_bytes, hist_bytes, lab_bytes, buf_bytes;
+  int graph_bytes, hist_bytes, lab_bytes, buf_bytes, cell_bytes;
 };
+
+// Cells of the last two positions (combinatorial counting): a relation word to
+// the k-2 chosen vertices has 2(k-2) bits.
+template <int K>
+constexpr int kCells = 1 << (2 * (K - 2));
 
 // Persistent enumerator.  A thread block works on one graph at a time: its
 // warps take that graph's items from the graph's queue; when the queue is
 // empty the block flushes its shared histogram, picks the next graph that still
 // has items and (GC) copies that graph's CSR into shared memory.
-template <int K, bool GC, bool LS>
+template <int K, bool GC, bool LS, bool COMB>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_cur_g;
@@ -310,16 +315,26 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   int32_t* s_urow = (int32_t*)sp;
   uint32_t* s_ucol = (uint32_t*)(sp + (GC ? ((a.nmax + 1) * 4 + 15) / 16 * 16 : 0));
   sp += a.graph_bytes;
-  uint32_t* s_hist = (uint32_t*)sp;
+  int32_t* s_hist = (int32_t*)sp;
   sp += a.hist_bytes;
-  unsigned char* mine = sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes);
+  unsigned char* mine =
+      sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
   LabT<K>* lab = LS ? (LabT<K>*)mine
                     : (LabT<K>*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.nmax;
   uint16_t* buf = (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
+  // combinatorial mode: per-cell counts (choices in the low, tail in the high
+  // 16 bits), the list of non-empty cells, and its length
+  uint32_t* ct = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes);
+  uint16_t* cl = (uint16_t*)(ct + kCells<K>);
+  int* ncell = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + a.cell_bytes - 16);
   const uint32_t C = a.classes;
 
   if (LS)
     for (int i = lane; i < a.nmax; i += 32) lab[i] = 0;
+  if (COMB) {
+    for (int i = lane; i < kCells<K>; i += 32) ct[i] = 0;
+    if (lane == 0) *ncell = 0;
+  }
   if (K <= 5)
     for (int i = tid; i < (int)C; i += blockDim.x) s_hist[i] = 0;
   if (tid == 0) s_cur_g = (int)(((int64_t)blockIdx.x * a.G) / gridDim.x);
@@ -351,22 +366,121 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     const int ib = a.item_off[(int64_t)g * a.nmax];
     const int ie = a.item_off[(int64_t)(g + 1) * a.nmax];
 
-    // Add `cnt` subgraphs of class `id` (called by one lane per group).
-    auto hadd = [&](uint32_t id, uint32_t cnt) {
+    // Add `delta` (may be negative in the combinatorial corrections) to class
+    // `id`.  Shared 32-bit counters spill +-2^29 to the graph's 64-bit counter
+    // (two's complement), large deltas go there directly, so no counter wraps.
+    auto hadd = [&](uint32_t id, long long delta) {
       if (id >= C) {
         atomicOr(w.err, kErrStackOverflow);
         return;
       }
-      if (K <= 5) {
-        const uint32_t old = atomicAdd(&s_hist[id], cnt);
-        if (old < 0x80000000u && old + cnt >= 0x80000000u) {
-          // spill 2^31 to the graph's 64-bit counter so the 32-bit one never wraps
-          atomicSub(&s_hist[id], 0x80000000u);
-          atomicAdd(&ghist[id], 0x80000000ull);
+      if (K <= 5 && delta < (1ll << 20) && delta > -(1ll << 20)) {
+        const int d = (int)delta;
+        const int old = atomicAdd(&s_hist[id], d);
+        const long long now = (long long)old + d;
+        if (old < (1 << 29) && now >= (1 << 29)) {
+          atomicSub(&s_hist[id], 1 << 29);
+          atomicAdd(&ghist[id], 1ull << 29);
+        } else if (old > -(1 << 29) && now <= -(1 << 29)) {
+          atomicAdd(&s_hist[id], 1 << 29);
+          atomicAdd(&ghist[id], (unsigned long long)(-(1ll << 29)));
         }
       } else {
-        atomicAdd(&ghist[id], (unsigned long long)cnt);
+        atomicAdd(&ghist[id], (unsigned long long)delta);
       }
+    };
+
+    // Combinatorial counting of the last two positions (Algorithm 1 of Sec. 3
+    // on the enumerator's (k-2)-set X with candidate list E = buf[c, e) whose
+    // choices are buf[c, ce)): the k-sets below X are the pairs {y, z}, y a
+    // choice and z after it in E, plus {y, u} with u an exclusive neighbour of
+    // y.  Without an arc between y and z the class depends only on the cells
+    // (relation words to X) of y and z, so those pairs are counted per cell
+    // pair; arcs inside E are corrected one by one; {y, u} depends only on y's
+    // cell and the arc code between y and u.
+    auto pair_level = [&](int c, int ce, int e, uint32_t P) {
+      constexpr int NB = 2 * (K - 2);
+      constexpr uint32_t LM = (1u << NB) - 1u;
+      constexpr uint32_t INC = 1u << NB, INT = 2u << NB;
+      constexpr int OFF2 = (K - 2) * (K - 3), OFF1 = (K - 1) * (K - 2);
+      // 1. cells of the choices and of the tail; flag E's members
+      for (int b = c; b < e; b += 32) {
+        const int i = b + lane;
+        const bool v = i < e;
+        uint32_t lam = 0, tag = 0xFFFFFFFFu;
+        bool inc = false;
+        if (v) {
+          const int u = buf[i];
+          const uint32_t l0 = lab[u];
+          lam = l0 & LM;
+          inc = i < ce;
+          lab[u] = (LabT<K>)(l0 | (inc ? INC : INT));
+          tag = lam | (inc ? 0x10000u : 0u);
+        }
+        const unsigned peers = __match_any_sync(kFull, tag);
+        if (v && lane == __ffs(peers) - 1) {
+          const uint32_t old = atomicAdd(&ct[lam], (uint32_t)__popc(peers) << (inc ? 0 : 16));
+          if (old == 0) cl[atomicAdd(ncell, 1)] = (uint16_t)lam;
+        }
+      }
+      __syncwarp();
+      const int r = *ncell;
+      // 2. pairs without an arc, per cell pair
+      for (int ia = 0; ia < r; ++ia) {
+        const uint32_t la = cl[ia];
+        const uint32_t pa = ct[la];
+        const long long ca = pa & 0xFFFFu, ta = pa >> 16;
+        for (int ib = ia + lane; ib < r; ib += 32) {
+          const uint32_t lb = cl[ib];
+          const uint32_t pb = ct[lb];
+          const long long cb = pb & 0xFFFFu, tb = pb >> 16;
+          const long long cnt = ia == ib ? ca * (ca - 1) / 2 + ca * ta : ca * cb + ca * tb + cb * ta;
+          if (cnt) hadd(__ldg(&a.table[P | (la << OFF2) | (lb << OFF1)]), cnt);
+        }
+      }
+      // 3. each choice's row: arcs inside E and exclusive neighbours by arc code
+      for (int i = c; i < ce; ++i) {
+        const int y = buf[i];
+        const uint32_t base = P | ((uint32_t)(lab[y] & LM) << OFF2);
+        const int rs = w.urow[y], re = w.urow[y + 1];
+        const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
+        int n1 = 0, n2 = 0, n3 = 0;
+        for (int b = start; b < re; b += 32) {
+          const int j = b + lane;
+          bool ex = false;
+          uint32_t code = 0;
+          if (j < re) {
+            const uint32_t ent = w.ucol[j];
+            const int u = (int)(ent & kVertexMask);
+            code = ent >> 30;
+            if (u > w.root) {
+              const uint32_t lu = lab[u];
+              ex = lu == 0;
+              if ((lu & INT) || ((lu & INC) && u > y)) {
+                const uint32_t cu = lu & LM;
+                hadd(__ldg(&a.table[base | ((cu | (code << NB)) << OFF1)]), 1);
+                hadd(__ldg(&a.table[base | (cu << OFF1)]), -1);
+              }
+            }
+          }
+          n1 += __popc(__ballot_sync(kFull, ex && code == 1));
+          n2 += __popc(__ballot_sync(kFull, ex && code == 2));
+          n3 += __popc(__ballot_sync(kFull, ex && code == 3));
+        }
+        if (lane < 3) {
+          const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
+          if (cnt) hadd(__ldg(&a.table[base | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+        }
+      }
+      // 4. clear flags and cells
+      for (int b = c; b < e; b += 32) {
+        const int i = b + lane;
+        if (i < e) lab[buf[i]] &= (LabT<K>)~(INC | INT);
+      }
+      for (int ia = lane; ia < r; ia += 32) ct[cl[ia]] = 0;
+      __syncwarp();
+      if (lane == 0) *ncell = 0;
+      __syncwarp();
     };
 
     while (true) {
@@ -413,7 +527,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         const int ce = __shfl_sync(kFull, s_ce, L);
         const int e = __shfl_sync(kFull, s_e, L);
         const uint32_t key = __shfl_sync(kFull, s_key, L);
-        if (L == K - 1) {
+        if (COMB && L == K - 2) {
+          pair_level(c, ce, e, key);
+          if (L == 1) break;
+          L -= 1;
+          pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+          continue;
+        }
+        if (!COMB && L == K - 1) {
           // leaves: every remaining candidate completes a k-set.  Leaves with
           // the same relation word to the k-1 chosen vertices lie in the same
           // cell of the partition of the set's neighbourhood (Sec. 2) and so in
@@ -472,9 +593,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     __syncthreads();
     if (K <= 5) {
       for (int i = tid; i < (int)C; i += blockDim.x) {
-        const uint32_t x = s_hist[i];
+        const int32_t x = s_hist[i];
         if (x) {
-          atomicAdd(&ghist[i], (unsigned long long)x);
+          atomicAdd(&ghist[i], (unsigned long long)(long long)x);
           s_hist[i] = 0;
         }
       }
@@ -500,18 +621,23 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
 
 static size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-template <int K>
-static const void* pick_kernel_k(bool gc, bool ls) {
-  if (gc) return ls ? (const void*)k_count<K, true, true> : (const void*)k_count<K, true, false>;
-  return ls ? (const void*)k_count<K, false, true> : (const void*)k_count<K, false, false>;
+template <int K, bool CB>
+static const void* pick_kernel_kc(bool gc, bool ls) {
+  if (gc) return ls ? (const void*)k_count<K, true, true, CB> : (const void*)k_count<K, true, false, CB>;
+  return ls ? (const void*)k_count<K, false, true, CB> : (const void*)k_count<K, false, false, CB>;
 }
 
-static const void* pick_kernel(int K, bool gc, bool ls) {
+template <int K>
+static const void* pick_kernel_k(bool gc, bool ls, bool cb) {
+  return cb ? pick_kernel_kc<K, true>(gc, ls) : pick_kernel_kc<K, false>(gc, ls);
+}
+
+static const void* pick_kernel(int K, bool gc, bool ls, bool cb) {
   switch (K) {
-    case 3: return pick_kernel_k<3>(gc, ls);
-    case 4: return pick_kernel_k<4>(gc, ls);
-    case 5: return pick_kernel_k<5>(gc, ls);
-    default: return pick_kernel_k<6>(gc, ls);
+    case 3: return pick_kernel_k<3>(gc, ls, cb);
+    case 4: return pick_kernel_k<4>(gc, ls, cb);
+    case 5: return pick_kernel_k<5>(gc, ls, cb);
+    default: return pick_kernel_k<6>(gc, ls, cb);
   }
 }
 
@@ -523,6 +649,7 @@ mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_
   t.split_scale = 0.0;
   t.warps_per_block = warps_per_block;
   t.stack_cap = 0;
+  t.method = MT_METHOD_ENUMERATE;
   const bool plain = split_cost == 0.0;
   MT_TRY(count_configure_tuned(p, K, G, nmax, dmax, fwd_bound, entry_stride, classes,
                                plain && warps_per_block == 0 ? nullptr : &t));
@@ -547,8 +674,12 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->cap = (tuning && tuning->stack_cap > 0) ? tuning->stack_cap : (K - 1) * std::max(dmax, 1) + 32;
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
+  p->comb = tuning && tuning->method == MT_METHOD_CELLS;
   const size_t lab_bytes = round16((size_t)nmax * (K <= 5 ? 1 : 2));
-  const size_t buf_bytes = round16((size_t)p->cap * 2);
+  const size_t cells = (size_t)1 << (2 * (K - 2));
+  const size_t cell_bytes =
+      p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 16 : 0;
+  const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes;
   const size_t hist_bytes = K <= 5 ? round16((size_t)classes * 4) : 0;
   const size_t graph_bytes = round16((size_t)(nmax + 1) * 4) + round16((size_t)p->nu_cap * 4);
   int dev = 0, sms = 0, max_smem = 0;
@@ -584,8 +715,9 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->graph_bytes = p->gcache ? graph_bytes : 0;
   p->hist_bytes = hist_bytes;
   p->lab_bytes = lab_bytes;
-  p->buf_bytes = buf_bytes;
-  const void* kern = pick_kernel(K, p->gcache, p->lab_smem);
+  p->buf_bytes = buf_bytes - cell_bytes;
+  p->cell_bytes = cell_bytes;
+  const void* kern = pick_kernel(K, p->gcache, p->lab_smem, p->comb);
   MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)p->smem_bytes));
   int occ = 0;
@@ -613,6 +745,17 @@ uint32_t* count_err_ptr(const CountPlan& p, void* ws) {
 }
 uint32_t* count_nitems_ptr(const CountPlan& p, void* ws) {
   return (uint32_t*)((char*)ws + p.off_cnt) + (size_t)p.G * p.nmax;
+}
+
+template <int K, bool CB>
+static void launch_count(const CountPlan& p, const CountArgs& a, unsigned threads, cudaStream_t s) {
+  if (p.gcache) {
+    if (p.lab_smem) k_count<K, true, true, CB><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+    else k_count<K, true, false, CB><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+  } else {
+    if (p.lab_smem) k_count<K, false, true, CB><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+    else k_count<K, false, false, CB><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+  }
 }
 
 template <int K>
@@ -663,14 +806,10 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
   a.hist_bytes = (int)p.hist_bytes;
   a.lab_bytes = (int)p.lab_bytes;
   a.buf_bytes = (int)p.buf_bytes;
+  a.cell_bytes = (int)p.cell_bytes;
   const unsigned threads = p.warps_per_block * 32;
-  if (p.gcache) {
-    if (p.lab_smem) k_count<K, true, true><<<p.blocks, threads, p.smem_bytes, s>>>(a);
-    else k_count<K, true, false><<<p.blocks, threads, p.smem_bytes, s>>>(a);
-  } else {
-    if (p.lab_smem) k_count<K, false, true><<<p.blocks, threads, p.smem_bytes, s>>>(a);
-    else k_count<K, false, false><<<p.blocks, threads, p.smem_bytes, s>>>(a);
-  }
+  if (p.comb) launch_count<K, true>(p, a, threads, s);
+  else launch_count<K, false>(p, a, threads, s);
   return cudaGetLastError();
 }
 
@@ -775,7 +914,8 @@ mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
   if (!g || !t || !hist) return MT_EINVAL;
   if (tuning && (tuning->split_cost < 0 || tuning->split_scale < 0 ||
                  tuning->warps_per_block < 0 || tuning->warps_per_block > 32 ||
-                 tuning->stack_cap < 0 || tuning->stack_cap > 65535))
+                 tuning->stack_cap < 0 || tuning->stack_cap > 65535 ||
+                 tuning->method < 0 || tuning->method > 1))
     return MT_EINVAL;
   return count_one(g, t, hist, 0, g->n, tuning, (cudaStream_t)stream);
 }

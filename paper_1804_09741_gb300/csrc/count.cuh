@@ -22,7 +22,8 @@ struct CountPlan {
   bool lab_smem = true;      // relation words in shared memory (else global slabs)
   bool gcache = true;        // the current graph's CSR copied into shared memory
   int nu_cap = 0;            // capacity of that copy (undirected entries)
-  size_t graph_bytes = 0, hist_bytes = 0, lab_bytes = 0, buf_bytes = 0;
+  size_t graph_bytes = 0, hist_bytes = 0, lab_bytes = 0, buf_bytes = 0, cell_bytes = 0;
+  bool comb = false;         // count the last two positions by cells (Algorithm 1)
   int cap = 0;              // stack entries per warp
   size_t smem_bytes = 0;
   uint64_t items_max = 0;

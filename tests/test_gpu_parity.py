@@ -31,9 +31,12 @@ def tables(lib):
     return get
 
 
-def gpu_hist(lib, t, g, via="host"):
+def gpu_hist(lib, t, g, via="host", method=0):
     dg = lib.graph_from(g)
-    if via == "host":
+    if method:
+        h = lib.to_numpy_u64(lib.count_tuned(dg, t, method=method))
+        assert lib.count_stats(dg)[1] == 0
+    elif via == "host":
         h = lib.count_host(dg, t)
     else:
         h = lib.to_numpy_u64(lib.count(dg, t))
@@ -42,8 +45,11 @@ def gpu_hist(lib, t, g, via="host"):
     return h, dg
 
 
-def check_against_oracle(lib, t, g, k, via="host"):
-    h, _ = gpu_hist(lib, t, g, via)
+METHODS = [0, 1]  # per-subgraph classification, cell-pair counting
+
+
+def check_against_oracle(lib, t, g, k, via="host", method=0):
+    h, _ = gpu_hist(lib, t, g, via, method)
     want, sets = oracle.count(g, k)
     assert int(h.sum()) == sets
     np.testing.assert_array_equal(h, oracle_dense(want, t.class_masks()))
@@ -92,30 +98,48 @@ def test_table_k6_classes_and_sampled_keys(lib, tables):
 # ------------------------------------------------------------------ counting (K2)
 
 
+@pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_small_random_digraphs(lib, tables, k, seed):
+def test_small_random_digraphs(lib, tables, k, seed, method):
     n = [14, 22, 30][seed]
     g = syn.random_small_digraph(n, [0.3, 0.15, 0.1][seed], 0.3, seed)
-    check_against_oracle(lib, tables(k), g, k, via="host" if seed % 2 else "device")
+    check_against_oracle(lib, tables(k), g, k, via="host" if seed % 2 else "device",
+                         method=method)
 
 
+@pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
-def test_closed_form_families_and_edges(lib, tables, k):
+def test_closed_form_families_and_edges(lib, tables, k, method):
     t = tables(k)
     for g in [syn.complete_digraph(9), syn.directed_cycle(13), syn.bidirected_path(12),
               syn.out_star(40), syn.empty_graph(10), syn.empty_graph(1), syn.complete_digraph(k - 1),
               syn.reverse(syn.out_star(33)),
               syn.disjoint_union(syn.complete_digraph(7), syn.empty_graph(5))]:
-        check_against_oracle(lib, t, g, k)
+        check_against_oracle(lib, t, g, k, method=method)
 
 
+@pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
-def test_medium_power_law_graphs(lib, tables, k):
+def test_medium_power_law_graphs(lib, tables, k, method):
     # several tiles per row and ragged tails: hubs of degree ~60-100
     n, m = {3: (900, 4000), 4: (600, 2400), 5: (300, 1000), 6: (160, 420)}[k]
     g = syn.chung_lu_digraph(n, m, 2.2, None, 0.15, 10 + k)
-    check_against_oracle(lib, tables(k), g, k)
+    check_against_oracle(lib, tables(k), g, k, method=method)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("split", [1.0, 1e12])
+@pytest.mark.parametrize("wpb", [1, 16])
+def test_cells_work_splitting_is_exact(lib, tables, k, split, wpb):
+    """The cell method under every split (k = 4 splits exactly at its pair level)."""
+    n, m = {3: (400, 1500), 4: (300, 1100), 5: (150, 450), 6: (90, 220)}[k]
+    g = syn.chung_lu_digraph(n, m, 2.1, None, 0.2, 78)
+    t = tables(k)
+    dg = lib.graph_from(g)
+    h = lib.to_numpy_u64(lib.count_tuned(dg, t, split, wpb, method=1))
+    assert lib.count_stats(dg)[1] == 0
+    np.testing.assert_array_equal(h, oracle_dense(oracle.count(g, k)[0], t.class_masks()))
 
 
 @pytest.mark.parametrize("k", [4, 5, 6])
@@ -135,14 +159,16 @@ def test_work_splitting_is_exact(lib, tables, k, split, wpb):
     np.testing.assert_array_equal(h, oracle_dense(want, t.class_masks()))
 
 
-def test_workload_uniform_k3_full(lib, tables):
+@pytest.mark.parametrize("method", METHODS)
+def test_workload_uniform_k3_full(lib, tables, method):
     g = syn.workload_graph("uniform_k3")
-    check_against_oracle(lib, tables(3), g, 3, via="device")
+    check_against_oracle(lib, tables(3), g, 3, via="device", method=method)
 
 
-def test_workload_chunglu_k4_full(lib, tables):
+@pytest.mark.parametrize("method", METHODS)
+def test_workload_chunglu_k4_full(lib, tables, method):
     g = syn.workload_graph("chunglu_k4")
-    check_against_oracle(lib, tables(4), g, 4, via="device")
+    check_against_oracle(lib, tables(4), g, 4, via="device", method=method)
 
 
 SAMPLES = {
@@ -173,6 +199,10 @@ def test_full_size_root_samples_and_partition(lib, tables, name):
     nosplit = lib.to_numpy_u64(lib.count_tuned(dg, t, 1e15, 8))
     np.testing.assert_array_equal(nosplit, full)
     assert lib.count_stats(dg)[1] == 0
+    # the cell method counts the same histogram at full size
+    cells = lib.to_numpy_u64(lib.count_tuned(dg, t, method=1))
+    assert lib.count_stats(dg)[1] == 0
+    np.testing.assert_array_equal(cells, full)
 
 
 # ------------------------------------------------------------------ randomiser (K3)
@@ -214,14 +244,15 @@ def test_duplicate_arc_rejected_on_device(lib):
 # ------------------------------------------------------------------ batch (a7-a9) + z (K5)
 
 
+@pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("k,n,m,R", [(4, 200, 700, 6), (5, 120, 380, 5), (6, 70, 180, 4),
                                      (3, 300, 1500, 9)])
-def test_batch_small_vs_oracle(lib, tables, k, n, m, R):
+def test_batch_small_vs_oracle(lib, tables, k, n, m, R, method):
     g = syn.chung_lu_digraph(n, m, 2.3, None, 0.1, 100 + k)
     t = tables(k)
     dg = lib.graph_from(g)
     seeds = np.arange(1, R + 1, dtype=np.uint64)
-    b = lib.Batch(dg, t, R, 10 * g.m)
+    b = lib.Batch(dg, t, R, 10 * g.m, lib.make_tuning(method=method) if method else None)
     for rep in range(2):  # second run replays the captured graph
         hists, z = b.run(seeds)
         hists = lib.to_numpy_u64(hists)
@@ -235,6 +266,8 @@ def test_batch_small_vs_oracle(lib, tables, k, n, m, R):
             np.testing.assert_array_equal(hists[r + 1], oracle_dense(oracle.count(gr, k)[0], cm))
         zo = oracle.zscores(hists[0], hists[1:])
         np.testing.assert_array_equal(z, zo)  # same float64 operations in the same order
+    if method:
+        return
     # host buffers through the one-shot entry point
     h2, z2 = lib.count_batch(dg, t, seeds, 10 * g.m)
     np.testing.assert_array_equal(h2, hists)
