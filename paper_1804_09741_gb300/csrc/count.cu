@@ -327,12 +327,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   uint32_t* ct = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes);
   uint16_t* cl = (uint16_t*)(ct + kCells<K>);
   int* ncell = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + a.cell_bytes - 16);
+  uint32_t* xc = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + a.cell_bytes - 16 - 384);
   const uint32_t C = a.classes;
 
   if (LS)
     for (int i = lane; i < a.nmax; i += 32) lab[i] = 0;
   if (COMB) {
     for (int i = lane; i < kCells<K>; i += 32) ct[i] = 0;
+    for (int i = lane; i < 96; i += 32) xc[i] = 0;
     if (lane == 0) *ncell = 0;
   }
   if (K <= 5)
@@ -438,39 +440,68 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           if (cnt) hadd(__ldg(&a.table[P | (la << OFF2) | (lb << OFF1)]), cnt);
         }
       }
-      // 3. each choice's row: arcs inside E and exclusive neighbours by arc code
-      for (int i = c; i < ce; ++i) {
-        const int y = buf[i];
-        const uint32_t base = P | ((uint32_t)(lab[y] & LM) << OFF2);
-        const int rs = w.urow[y], re = w.urow[y + 1];
-        const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
-        int n1 = 0, n2 = 0, n3 = 0;
-        for (int b = start; b < re; b += 32) {
-          const int j = b + lane;
+      // 3. the choices' rows, 32 choices at a time with their rows (entries above
+      //    the root) concatenated over the lanes: arcs inside E are corrected,
+      //    exclusive neighbours are counted per (choice, arc code)
+      for (int cb = c; cb < ce; cb += 32) {
+        const int i = cb + lane;
+        const bool vy = i < ce;
+        int y = 0, rs = 0, len = 0;
+        uint32_t ly = 0;
+        if (vy) {
+          y = buf[i];
+          const int r0 = w.urow[y], r1 = w.urow[y + 1];
+          rs = first_above_p(w.ucol, r0, r1, w.root);
+          len = r1 - rs;
+          ly = lab[y] & LM;
+        }
+        const int incl = warp_incl_scan(len);
+        const int pre = incl - len;
+        const int total = __shfl_sync(kFull, incl, 31);
+        for (int q0 = 0; q0 < total; q0 += 32) {
+          const int q = q0 + lane;
+          // the lane's choice: the largest s with pre[s] <= q
+          int sidx = 0;
+          for (int step = 16; step; step >>= 1) {
+            const int cand = sidx + step;
+            const int pc = __shfl_sync(kFull, pre, cand & 31);
+            if (cand <= 31 && pc <= q) sidx = cand;
+          }
+          const int ys = __shfl_sync(kFull, y, sidx);
+          const int rss = __shfl_sync(kFull, rs, sidx);
+          const int ps = __shfl_sync(kFull, pre, sidx);
+          const uint32_t lys = __shfl_sync(kFull, ly, sidx);
           bool ex = false;
           uint32_t code = 0;
-          if (j < re) {
-            const uint32_t ent = w.ucol[j];
+          if (q < total) {
+            const uint32_t ent = w.ucol[rss + (q - ps)];
             const int u = (int)(ent & kVertexMask);
             code = ent >> 30;
-            if (u > w.root) {
-              const uint32_t lu = lab[u];
-              ex = lu == 0;
-              if ((lu & INT) || ((lu & INC) && u > y)) {
-                const uint32_t cu = lu & LM;
-                hadd(__ldg(&a.table[base | ((cu | (code << NB)) << OFF1)]), 1);
-                hadd(__ldg(&a.table[base | (cu << OFF1)]), -1);
-              }
+            const uint32_t lu = lab[u];
+            ex = lu == 0;
+            if ((lu & INT) || ((lu & INC) && u > ys)) {
+              const uint32_t bs = P | (lys << OFF2);
+              const uint32_t cu = lu & LM;
+              hadd(__ldg(&a.table[bs | ((cu | (code << NB)) << OFF1)]), 1);
+              hadd(__ldg(&a.table[bs | (cu << OFF1)]), -1);
             }
           }
-          n1 += __popc(__ballot_sync(kFull, ex && code == 1));
-          n2 += __popc(__ballot_sync(kFull, ex && code == 2));
-          n3 += __popc(__ballot_sync(kFull, ex && code == 3));
+          const uint32_t tag = ex ? (uint32_t)(sidx * 4) + code : 0xFFFFFFFFu;
+          const unsigned peers = __match_any_sync(kFull, tag);
+          if (ex && lane == __ffs(peers) - 1) atomicAdd(&xc[sidx * 3 + code - 1], (uint32_t)__popc(peers));
         }
-        if (lane < 3) {
-          const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
-          if (cnt) hadd(__ldg(&a.table[base | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+        __syncwarp();
+        if (vy) {
+          const uint32_t bs = P | (ly << OFF2);
+          for (int cd = 1; cd <= 3; ++cd) {
+            const uint32_t cnt = xc[lane * 3 + cd - 1];
+            if (cnt) {
+              hadd(__ldg(&a.table[bs | (((uint32_t)cd << NB) << OFF1)]), cnt);
+              xc[lane * 3 + cd - 1] = 0;
+            }
+          }
         }
+        __syncwarp();
       }
       // 4. clear flags and cells
       for (int b = c; b < e; b += 32) {
@@ -678,7 +709,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   const size_t lab_bytes = round16((size_t)nmax * (K <= 5 ? 1 : 2));
   const size_t cells = (size_t)1 << (2 * (K - 2));
   const size_t cell_bytes =
-      p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 16 : 0;
+      p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 384 + 16 : 0;
   const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes;
   const size_t hist_bytes = K <= 5 ? round16((size_t)classes * 4) : 0;
   const size_t graph_bytes = round16((size_t)(nmax + 1) * 4) + round16((size_t)p->nu_cap * 4);
