@@ -142,7 +142,7 @@ def _config(args, w, world):
          "gamma": w.get("gamma"), "dmax": w.get("dmax"), "reciprocity": w.get("recip"),
          "null_graphs": nulls, "swaps_per_null": 10 * w["m"] if nulls else 0,
          "graphs_per_step": 1 + nulls, "parallelism": f"replicas{world}",
-         "l2": "flushed between timed steps (256 MiB write)"}
+         "l2": "flushed between timed steps (256 MiB write)", "method": args.method}
     return c
 
 
@@ -175,8 +175,10 @@ def run_ours(args, world, rank, local):
     seeds = shard.rank_seeds(R, rank) if R else None
     swaps = 10 * g.m
 
+    method = mt.METHOD_CELLS if args.method == "cells" else mt.METHOD_ENUMERATE
+    tuning = mt.make_tuning(method=method) if method else None
     if R:
-        batch = mt.Batch(dg, table, R, swaps)
+        batch = mt.Batch(dg, table, R, swaps, tuning)
         hists = torch.empty((R + 1, C), dtype=torch.int64, device="cuda")
         z = torch.empty(C, dtype=torch.float64, device="cuda")
 
@@ -187,7 +189,10 @@ def run_ours(args, world, rank, local):
         hists = torch.empty(C, dtype=torch.int64, device="cuda")
 
         def step():
-            mt.count(dg, table, hists)
+            if tuning is None:
+                mt.count(dg, table, hists)
+            else:
+                mt.count_tuned(dg, table, out=hists, method=method)
         launches_per_step = 5
 
     for _ in range(max(args.warmup, 3)):
@@ -277,7 +282,8 @@ def run_ours(args, world, rank, local):
                                    f"({src} sm_max_mhz)"}
 
     extra = {}
-    if rank == 0 and not args.no_extra and args.workload == "nullmodel_k5" and args.nulls is None:
+    if (rank == 0 and not args.no_extra and args.workload == "nullmodel_k5" and args.nulls is None
+            and args.method == "enumerate"):
         extra["plain_vs_batched"] = measure_plain_vs_batched(
             mt, torch, dg, table, g, (1 + R) / (total_ms / args.steps / 1000.0))
         extra["k6_batch"] = measure_k6(mt, torch)
@@ -287,6 +293,7 @@ def run_ours(args, world, rank, local):
             "note": "same workloads counted with MT_METHOD_CELLS (Algorithm 1 of Sec. 3: the "
                     "last two vertices counted per cell pair); histograms identical"}
         extra["serving"] = measure_serving(mt, torch, {5: table})
+        extra["serving_cells"] = measure_serving(mt, torch, {5: table}, method=1)
 
     if rank == 0:
         line = {"metric": "k-subgraphs classified/s", "value": value, "unit": "subgraphs/s",
@@ -424,7 +431,7 @@ def serving_requests(num, seed):
     return out
 
 
-def measure_serving(mt, torch, have_tables, num=32, seed=0):
+def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0):
     """Continuous-batching server on a seeded stream of mixed-k requests:
     closed-loop capacity first, then Poisson arrivals at 80% of it."""
     from paper_1804_09741_gb300.server import Server, poisson_arrivals, run_stream
@@ -433,7 +440,7 @@ def measure_serving(mt, torch, have_tables, num=32, seed=0):
     for k in (3, 4, 5, 6):
         if k not in tables:
             tables[k] = mt.table_build(k)
-    srv = Server(tables, memory_budget=16 << 30, max_slots=32, round_cost=4e8)
+    srv = Server(tables, memory_budget=16 << 30, max_slots=32, round_cost=4e8, method=method)
     run_stream(srv, reqs[:4])  # warm-up
     res, lat, wall = run_stream(srv, reqs)
     cap = num / wall
@@ -448,7 +455,7 @@ def measure_serving(mt, torch, have_tables, num=32, seed=0):
             "p99_ms": float(np.percentile(lat, 99)), "subgraphs_per_s": sub / wall2,
             "requests": num, "k_mix": {str(k): ks.count(k) for k in (3, 4, 5, 6)},
             "n_range": [int(min(g.n for _, g in reqs)), int(max(g.n for _, g in reqs))],
-            "all_ok": ok}
+            "all_ok": ok, "method": "cells" if method else "enumerate"}
 
 
 # Algorithmic integer operations per classified subgraph in the leaf loop:
@@ -466,6 +473,8 @@ def main():
     ap.add_argument("--workload", default="nullmodel_k5", choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--method", default="enumerate", choices=["enumerate", "cells"],
+                    help="counting method of the main measurement (recorded in config)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the k=6 batch, plain-vs-batched and serving measurements")
     ap.add_argument("--nulls", type=int, default=None,

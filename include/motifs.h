@@ -317,6 +317,10 @@ mt_status mt_server_step(mt_server* s, int32_t* completed, int32_t* active, int3
 mt_status mt_server_result(mt_server* s, uint64_t id, int32_t* state, uint64_t* hist,
                            double* latency_ms);
 
+/* Counting method of the rounds launched from now on (an mt_method; the
+ * default is MT_METHOD_ENUMERATE).  Results do not depend on it. */
+mt_status mt_server_set_method(mt_server* s, int method);
+
 /* Device bytes currently charged against the budget by active requests. */
 mt_status mt_server_used_bytes(const mt_server* s, size_t* used);
 

@@ -76,6 +76,7 @@ SIGNATURES = {
     "mt_server_step": (ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i32)]),
     "mt_server_result": (ctypes.c_int, [_vp, _u64, _P(_i32), _vp, _P(_f64)]),
     "mt_server_used_bytes": (ctypes.c_int, [_vp, _P(ctypes.c_size_t)]),
+    "mt_server_set_method": (ctypes.c_int, [_vp, ctypes.c_int]),
 }
 
 

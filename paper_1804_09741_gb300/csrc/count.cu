@@ -9,25 +9,32 @@
 // every remaining candidate completes one k-set.
 //
 // GPU mapping (one warp = one depth-first walk, lanes cooperate):
-//  * per warp a 16-bit "relation word" lab[u] for every vertex: bits 2p, 2p+1
-//    hold the A/B/C relation (Sec. 2) of u to the vertex at position p of the
-//    current set.  Pushing w at position p scans delta(w) coalesced (the
-//    row-scan strategy of Sec. 3.1, Algorithm 3), ORs its relation bits into
-//    lab[u] and, with one ballot, appends to the candidate stack every u whose
-//    word was zero (exclusive neighbour).  Popping clears the same bits.
+//  * per warp a "relation word" lab[u] for every vertex (8 bits for k <= 5, 16
+//    for k = 6): bits 2p, 2p+1 hold the A/B/C relation (Sec. 2) of u to the
+//    vertex at position p of the current set.  Pushing w at position p scans
+//    delta(w) above the root coalesced (the row-scan strategy of Sec. 3.1),
+//    ORs its relation bits into lab[u] and, with one ballot, appends to the
+//    candidate stack every u whose word was zero (exclusive neighbour).
+//    Popping clears the same bits;
 //  * candidate lists of all levels live in one per-warp stack: level p+1's list
 //    is the unused tail of level p's list followed by the newly appended
 //    exclusive neighbours, so no list is ever copied;
 //  * level state (cursor, ends, pushed vertex, key prefix) lives in registers of
 //    lane p and is read with shuffles;
-//  * the class key of a leaf u is the key prefix of the set OR lab[u] shifted to
-//    the last position: no per-subgraph adjacency test at all;
-//  * histograms: per-warp shared-memory counters for k <= 4 (13 / 199 classes),
-//    warp-aggregated (match_any) 64-bit global atomics for k = 5, 6.
+//  * choosing the (k-1)-th vertex y finishes its k-sets in place: y's row scan
+//    classifies the exclusive neighbours (their word is the arc code to y), and
+//    each remaining candidate's key is the key prefix OR its word shifted to the
+//    last position -- no per-subgraph adjacency test; equal keys of a batch of
+//    32 leaves share one table read (match_any);
+//  * MT_METHOD_CELLS stops one level earlier and counts the last two vertices
+//    per pair of cells (Algorithm 1 of Sec. 3; see pair_level below);
+//  * histograms: per-block shared-memory counters for k <= 5 (13 / 199 / 9,364
+//    classes), 64-bit global atomics for k = 6.
 //
 // Work items are (graph, root, first-level branch range) or, for expensive
 // branches, (graph, root, branch, second-level choice range); a planner sizes
-// them from per-branch cost estimates and warps take them from a global queue.
+// them from per-branch cost estimates.  Blocks work graph by graph, warps take
+// the items of the block's current graph from that graph's queue.
 #include <algorithm>
 #include <type_traits>
 
@@ -565,13 +572,52 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
           continue;
         }
-        if (!COMB && L == K - 1) {
-          // leaves: every remaining candidate completes a k-set.  Leaves with
-          // the same relation word to the k-1 chosen vertices lie in the same
-          // cell of the partition of the set's neighbourhood (Sec. 2) and so in
-          // the same class: one lane per cell reads the table and adds the
-          // cell's size.  Two batches of 32 are in flight.
-          for (int b = c; b < e; b += 64) {
+        if (!COMB && L == K - 2) {
+          // choosing the (k-1)-th vertex: its k-sets are classified right here.
+          if (c >= ce) {
+            if (L == 1) break;
+            L -= 1;
+            pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+            continue;
+          }
+          const int y = buf[c];
+          if (lane == L) s_c = c + 1;
+          const uint32_t P2 = key | ((uint32_t)lab[y] << (L * (L - 1)));
+          constexpr int OFF1 = (K - 1) * (K - 2);
+          constexpr int NB = 2 * (K - 2);
+          // (a) y's row: mark its relation bits; an exclusive neighbour u (no
+          //     relation to the first k-2 vertices) completes a k-set whose key
+          //     is fixed by the arc code between y and u
+          {
+            const int rs = w.urow[y], re = w.urow[y + 1];
+            const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
+            int n1 = 0, n2 = 0, n3 = 0;
+            for (int b = start; b < re; b += 32) {
+              const int j = b + lane;
+              bool ex = false;
+              uint32_t code = 0;
+              if (j < re) {
+                const uint32_t ent = w.ucol[j];
+                const int u = (int)(ent & kVertexMask);
+                code = ent >> 30;
+                if (u > w.root) {
+                  const LabT<K> old = lab[u];
+                  lab[u] = (LabT<K>)(old | (code << NB));
+                  ex = old == 0;
+                }
+              }
+              n1 += __popc(__ballot_sync(kFull, ex && code == 1));
+              n2 += __popc(__ballot_sync(kFull, ex && code == 2));
+              n3 += __popc(__ballot_sync(kFull, ex && code == 3));
+            }
+            __syncwarp();
+            if (lane < 3) {
+              const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
+              if (cnt) hadd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+            }
+          }
+          // (b) the tail buf[c+1, e): relation words now include y's bits
+          for (int b = c + 1; b < e; b += 64) {
             const int i0 = b + lane, i1 = b + 32 + lane;
             const bool v0 = i0 < e, v1 = i1 < e;
             const uint32_t l0 = v0 ? (uint32_t)lab[buf[i0]] : 0xFFFFFFFFu;
@@ -581,13 +627,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             const bool lead0 = v0 && lane == __ffs(p0) - 1;
             const bool lead1 = v1 && lane == __ffs(p1) - 1;
             uint32_t id0 = kNoClass, id1 = kNoClass;
-            if (lead0) id0 = __ldg(&a.table[key | (l0 << ((K - 1) * (K - 2)))]);
-            if (lead1) id1 = __ldg(&a.table[key | (l1 << ((K - 1) * (K - 2)))]);
+            if (lead0) id0 = __ldg(&a.table[P2 | (l0 << OFF1)]);
+            if (lead1) id1 = __ldg(&a.table[P2 | (l1 << OFF1)]);
             if (lead0) hadd(id0, __popc(p0));
             if (lead1) hadd(id1, __popc(p1));
           }
-          L -= 1;
-          pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+          // (c) unmark y
+          pop_vertex<K>(w, y, L);
           continue;
         }
         if (c < ce) {

@@ -10,8 +10,9 @@
 //
 // GPU mapping: one thread block per graph.  The arc array (src<<16 | dst) and an
 // open-addressing hash set of the present arcs sit in shared memory; the block
-// fills them in parallel and one thread then runs the attempts in order.  Many
-// graphs run side by side (the null-model batch).
+// fills them in parallel; warp 0 draws the positions of 32 attempts at a time
+// and one lane applies them in order.  Many graphs run side by side (the
+// null-model batch).
 //
 // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014, public-domain reference
 // generator): state advances by the golden gamma 0x9E3779B97F4A7C15, output =
@@ -105,30 +106,42 @@ __global__ void __launch_bounds__(512) k_randomize(RandArgs a) {
     while (atomicCAS(&hs.t[i], kEmpty, key) != kEmpty) i = (i + 1) & hs.mask;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && m > 0) {
+  // Warp 0: the 32 lanes draw the arc positions of the next 32 attempts (the
+  // SplitMix64 outputs do not depend on the graph), then lane 0 applies those
+  // attempts in order.
+  __shared__ uint32_t s_e[64];
+  if (threadIdx.x < 32 && m > 0) {
+    const int lane = threadIdx.x;
     const uint64_t seed = a.seeds[g];
     const uint64_t gamma = 0x9E3779B97F4A7C15ull;
     int64_t acc = 0;
-    for (uint64_t t = 0; t < a.swaps; ++t) {
-      const uint64_t r1 = sm64_mix(seed + (2 * t + 1) * gamma);
-      const uint64_t r2 = sm64_mix(seed + (2 * t + 2) * gamma);
-      const uint32_t e1 = (uint32_t)__umul64hi(r1, (uint64_t)m);
-      const uint32_t e2 = (uint32_t)__umul64hi(r2, (uint64_t)m);
-      if (e1 == e2) continue;
-      const uint32_t A = arcs[e1], B = arcs[e2];
-      const uint32_t sa = A >> 16, da = A & 0xFFFFu, sc = B >> 16, dc = B & 0xFFFFu;
-      if (sa == sc || da == dc || sa == dc || sc == da) continue;
-      const uint32_t n1 = (sa << 16) | dc, n2 = (sc << 16) | da;
-      if (hs.find(n1) >= 0 || hs.find(n2) >= 0) continue;
-      hs.erase_slot((uint32_t)hs.find(A));
-      hs.erase_slot((uint32_t)hs.find(B));
-      hs.insert(n1);
-      hs.insert(n2);
-      arcs[e1] = n1;
-      arcs[e2] = n2;
-      ++acc;
+    for (uint64_t t0 = 0; t0 < a.swaps; t0 += 32) {
+      const uint64_t t = t0 + lane;
+      s_e[lane] = (uint32_t)__umul64hi(sm64_mix(seed + (2 * t + 1) * gamma), (uint64_t)m);
+      s_e[32 + lane] = (uint32_t)__umul64hi(sm64_mix(seed + (2 * t + 2) * gamma), (uint64_t)m);
+      __syncwarp();
+      if (lane == 0) {
+        const int cnt = (int)((a.swaps - t0) < 32 ? (a.swaps - t0) : 32);
+        for (int j = 0; j < cnt; ++j) {
+          const uint32_t e1 = s_e[j], e2 = s_e[32 + j];
+          if (e1 == e2) continue;
+          const uint32_t A = arcs[e1], B = arcs[e2];
+          const uint32_t sa = A >> 16, da = A & 0xFFFFu, sc = B >> 16, dc = B & 0xFFFFu;
+          if (sa == sc || da == dc || sa == dc || sc == da) continue;
+          const uint32_t n1 = (sa << 16) | dc, n2 = (sc << 16) | da;
+          if (hs.find(n1) >= 0 || hs.find(n2) >= 0) continue;
+          hs.erase_slot((uint32_t)hs.find(A));
+          hs.erase_slot((uint32_t)hs.find(B));
+          hs.insert(n1);
+          hs.insert(n2);
+          arcs[e1] = n1;
+          arcs[e2] = n2;
+          ++acc;
+        }
+      }
+      __syncwarp();
     }
-    if (a.accepted) a.accepted[g] = acc;
+    if (lane == 0 && a.accepted) a.accepted[g] = acc;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < m; e += blockDim.x)

@@ -72,6 +72,7 @@ struct mt_server {
   size_t d_graphs_cap[4] = {0, 0, 0, 0};
   std::vector<uint64_t*> pinned_free[4];  // result buffers by k
   std::chrono::steady_clock::time_point t0;
+  int method = MT_METHOD_ENUMERATE;
 };
 
 namespace mt {
@@ -264,7 +265,14 @@ static mt_status step(mt_server* s, int32_t* completed) {
         fwd += c.r->g->nu / 2 + 1;
       }
       CountPlan p;
-      MT_TRY(count_configure(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C, 0.0, 0));
+      mt_tuning tun;
+      tun.split_cost = 0.0;
+      tun.split_scale = 0.0;
+      tun.warps_per_block = 0;
+      tun.stack_cap = 0;
+      tun.method = s->method;
+      MT_TRY(count_configure_tuned(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C,
+                                   s->method == MT_METHOD_ENUMERATE ? nullptr : &tun));
       MT_TRY(ensure_capacity(s, ki, p.ws_bytes, chunks.size()));
       DevGraph* hg = R.h_graphs + off;
       for (size_t i = 0; i < chunks.size(); ++i) {
@@ -378,6 +386,12 @@ mt_status mt_server_result(mt_server* s, uint64_t id, int32_t* state, uint64_t* 
     s->all.erase(it);
     delete r;
   }
+  return MT_OK;
+}
+
+mt_status mt_server_set_method(mt_server* s, int method) {
+  if (!s || (method != MT_METHOD_ENUMERATE && method != MT_METHOD_CELLS)) return MT_EINVAL;
+  s->method = method;
   return MT_OK;
 }
 

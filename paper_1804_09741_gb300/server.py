@@ -17,7 +17,7 @@ class Server:
     """Continuous-batching server over resident per-k tables."""
 
     def __init__(self, tables: dict, memory_budget: int = 8 << 30, max_slots: int = 64,
-                 round_cost: float = 4e8):
+                 round_cost: float = 4e8, method: int = 0):
         self.lib = load_library()
         self.tables = dict(tables)
         ts = [self.tables[k].handle if k in self.tables else None for k in (3, 4, 5, 6)]
@@ -25,6 +25,9 @@ class Server:
         _check(self.lib.mt_server_create(*ts, int(memory_budget), int(max_slots),
                                          float(round_cost), ctypes.byref(h)), "mt_server_create")
         self.handle = h.value
+        if method:
+            _check(self.lib.mt_server_set_method(self.handle, int(method)),
+                   "mt_server_set_method")
 
     def submit(self, k: int, g) -> int:
         rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)

@@ -20,7 +20,8 @@ def alone(mt, t, g):
     return mt.count_host(mt.graph_from(g), t)
 
 
-def test_mixed_stream_equals_alone(tables):
+@pytest.mark.parametrize("method", [0, 1])
+def test_mixed_stream_equals_alone(tables, method):
     import paper_1804_09741_gb300 as mt
     from paper_1804_09741_gb300.server import Server, poisson_arrivals, run_stream
     reqs = []
@@ -32,7 +33,7 @@ def test_mixed_stream_equals_alone(tables):
         reqs.append((k, g))
     reqs += [(4, syn.empty_graph(7)), (5, syn.empty_graph(1)), (6, syn.complete_digraph(5)),
              (3, syn.complete_digraph(9))]
-    srv = Server(tables, memory_budget=2 << 30, max_slots=8, round_cost=2e6)
+    srv = Server(tables, memory_budget=2 << 30, max_slots=8, round_cost=2e6, method=method)
     out, lat, wall = run_stream(srv, reqs, poisson_arrivals(len(reqs), 400.0, 1))
     for (k, g), (st, hist, status) in zip(reqs, out):
         assert st == 2, status
