@@ -177,6 +177,17 @@ def run_ours(args, world, rank, local):
 
     method = mt.METHOD_CELLS if args.method == "cells" else mt.METHOD_ENUMERATE
     tuning = mt.make_tuning(method=method) if method else None
+    tuned = None
+    if R and not args.no_autotune:
+        from paper_1804_09741_gb300 import autotune
+        t_tune = time.perf_counter()
+        tp = autotune.tune_batch(dg, table, g, swaps, probe_nulls=16, method=method,
+                                 cache_path=None)
+        tuning = mt.make_tuning(0.0, tp.warps_per_block, tp.split_scale, tp.stack_cap, method)
+        tuned = {"warps_per_block": tp.warps_per_block, "split_scale": tp.split_scale,
+                 "stack_cap": tp.stack_cap, "probe_count_ms": tp.ms,
+                 "tune_s": time.perf_counter() - t_tune,
+                 "source": "autotuner: 16-null probe batch, 8 candidates"}
     if R:
         batch = mt.Batch(dg, table, R, swaps, tuning)
         hists = torch.empty((R + 1, C), dtype=torch.int64, device="cuda")
@@ -307,6 +318,7 @@ def run_ours(args, world, rank, local):
                 "table_build_ms": table_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+        line["config"]["tuning"] = tuned or "automatic"
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
@@ -337,7 +349,7 @@ def measure_k6(mt, torch, steps=3, warmup=3):
     table_ms = 1000 * (time.perf_counter() - t0)
     dg = mt.graph_from(g)
     R = w["nulls"]
-    b = mt.Batch(dg, t, R, 10 * g.m)
+    b = mt.Batch(dg, t, R, 10 * g.m, _autotuned(mt, dg, t, g, 0))
     seeds = np.arange(1, R + 1, dtype=np.uint64)
     hists = torch.empty((R + 1, t.num_classes), dtype=torch.int64, device="cuda")
     z = torch.empty(t.num_classes, dtype=torch.float64, device="cuda")
@@ -356,6 +368,12 @@ def measure_k6(mt, torch, steps=3, warmup=3):
     return out
 
 
+def _autotuned(mt, dg, t, g, method):
+    from paper_1804_09741_gb300 import autotune
+    tp = autotune.tune_batch(dg, t, g, 10 * g.m, probe_nulls=16, method=method, cache_path=None)
+    return mt.make_tuning(0.0, tp.warps_per_block, tp.split_scale, tp.stack_cap, method)
+
+
 def measure_batch_method(mt, torch, name, table, method=1, steps=3, warmup=3):
     """A null-model batch counted with another counting method."""
     w = syn.WORKLOADS[name]
@@ -364,7 +382,7 @@ def measure_batch_method(mt, torch, name, table, method=1, steps=3, warmup=3):
     t = mt.table_build(w["k"]) if own else table
     dg = mt.graph_from(g)
     R = w["nulls"]
-    b = mt.Batch(dg, t, R, 10 * g.m, mt.make_tuning(method=method))
+    b = mt.Batch(dg, t, R, 10 * g.m, _autotuned(mt, dg, t, g, method))
     seeds = np.arange(1, R + 1, dtype=np.uint64)
     hists = torch.empty((R + 1, t.num_classes), dtype=torch.int64, device="cuda")
     z = torch.empty(t.num_classes, dtype=torch.float64, device="cuda")
@@ -473,6 +491,8 @@ def main():
     ap.add_argument("--workload", default="nullmodel_k5", choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the automatic launch instead of the autotuner's choice")
     ap.add_argument("--method", default="enumerate", choices=["enumerate", "cells"],
                     help="counting method of the main measurement (recorded in config)")
     ap.add_argument("--no-extra", action="store_true",

@@ -17,7 +17,7 @@ import os
 
 import numpy as np
 
-from . import count_stats, count_tuned, make_tuning, to_numpy_u64
+from . import count_stats, count_tuned, make_tuning, to_numpy_u64  # noqa: F401
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "motifs_gb300", "autotune.json")
 
@@ -94,6 +94,52 @@ def tune(dev_graph, table, graph=None, reps: int = 3, cache_path: str | None = D
         c.ms = _time(run, reps)
         if c.ms < best.ms:
             best = c
+    cache[key] = dataclasses.asdict(best)
+    save_cache(cache, cache_path)
+    return best
+
+
+def tune_batch(dev_graph, table, graph, swaps: int, probe_nulls: int = 16, method: int = 0,
+               reps: int = 2, cache_path: str | None = DEFAULT_CACHE,
+               force: bool = False) -> TuneParams:
+    """Best TuneParams for the null-model batch of this graph's degree profile,
+    timed on a probe batch of `probe_nulls` null graphs (the counting phase,
+    device events); every candidate's histograms must equal the automatic
+    launch's."""
+    import torch
+
+    from . import Batch
+
+    key = degree_profile(graph, table.k) + f"-batch-m{method}"
+    cache = load_cache(cache_path)
+    if not force and key in cache:
+        return TuneParams(**cache[key])
+    seeds = np.arange(1, probe_nulls + 1, dtype=np.uint64)
+    ref = None
+    best = None
+    for wpb in (16, 32):
+        for scale in (0.25, 0.5, 1.0, 2.0):
+            c = TuneParams(wpb, scale, 0)
+            tun = make_tuning(0.0, wpb, scale, 0, method)
+            b = Batch(dev_graph, table, probe_nulls, swaps, tun)
+            h, _ = b.run(seeds)
+            torch.cuda.synchronize()
+            if b.error() != 0:
+                b.free()
+                continue
+            hn = to_numpy_u64(h).copy()
+            if ref is None:
+                ref = hn
+            elif not np.array_equal(hn, ref):
+                raise RuntimeError(f"tuned batch {c} changed the histograms")
+            ts = []
+            for _ in range(reps):
+                b.run(seeds, h)
+                ts.append(b.phase_ms()[1])
+            c.ms = float(np.median(ts))
+            b.free()
+            if best is None or c.ms < best.ms:
+                best = c
     cache[key] = dataclasses.asdict(best)
     save_cache(cache, cache_path)
     return best

@@ -70,3 +70,18 @@ def test_autotuner_picks_a_valid_launch_and_caches_it(t5, tmp_path):
     h = mt.to_numpy_u64(mt.count_tuned(dg, t5, 0.0, p.warps_per_block, split_scale=p.split_scale,
                                        stack_cap=p.stack_cap))
     np.testing.assert_array_equal(h, mt.to_numpy_u64(mt.count(dg, t5)))
+
+
+def test_batch_autotuner_keeps_histograms(t5, tmp_path):
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300 import autotune
+    g = syn.chung_lu_digraph(300, 1000, 2.2, None, 0.1, 12)
+    dg = mt.graph_from(g)
+    path = str(tmp_path / "b.json")
+    p = autotune.tune_batch(dg, t5, g, 10 * g.m, probe_nulls=4, cache_path=path)
+    assert p.warps_per_block in (16, 32) and p.ms > 0
+    assert autotune.tune_batch(dg, t5, g, 10 * g.m, probe_nulls=4, cache_path=path) == p
+    seeds = np.arange(1, 5, dtype=np.uint64)
+    h0, _ = mt.Batch(dg, t5, 4, 10 * g.m).run(seeds)
+    h1, _ = mt.Batch(dg, t5, 4, 10 * g.m, p.tuning()).run(seeds)
+    np.testing.assert_array_equal(mt.to_numpy_u64(h0), mt.to_numpy_u64(h1))
