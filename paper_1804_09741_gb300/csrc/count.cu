@@ -215,14 +215,14 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int32_t* data, int count) 
 // ------------------------------------------------------------------ enumerator
 
 // Relation words: 2 bits per earlier position, k-1 positions -> 8 bits for k <= 5.
-template <int K>
+template <int K, bool CB>
 using LabT = typename std::conditional<(K <= 5), uint8_t, uint16_t>::type;
 
-template <int K>
+template <typename LT>
 struct WarpCtx {
   const int32_t* urow;   // shared-memory copy of the graph or global memory
   const uint32_t* ucol;
-  LabT<K>* lab;
+  LT* lab;
   uint16_t* buf;
   int cap;
   int root;
@@ -242,8 +242,8 @@ __device__ __forceinline__ int first_above_p(const uint32_t* ucol, int lo, int h
 // Push x at position p: OR its relation bits into lab[] of its neighbours above
 // the root and append the exclusive ones (relation word was zero) at stack
 // index e.  Returns the new end of the candidate list.
-template <int K>
-__device__ __forceinline__ int push_vertex(const WarpCtx<K>& w, int x, int p, int e) {
+template <typename LT>
+__device__ __forceinline__ int push_vertex(const WarpCtx<LT>& w, int x, int p, int e) {
   const int rs = w.urow[x], re = w.urow[x + 1];
   const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
   const unsigned lt = (1u << w.lane) - 1u;
@@ -256,8 +256,8 @@ __device__ __forceinline__ int push_vertex(const WarpCtx<K>& w, int x, int p, in
       const uint32_t ent = w.ucol[i];
       u = (int)(ent & kVertexMask);
       if (u > w.root) {
-        const LabT<K> old = w.lab[u];
-        w.lab[u] = (LabT<K>)(old | ((ent >> 30) << (2 * p)));
+        const LT old = w.lab[u];
+        w.lab[u] = (LT)(old | ((ent >> 30) << (2 * p)));
         ex = (old == 0);
       }
     }
@@ -275,11 +275,11 @@ __device__ __forceinline__ int push_vertex(const WarpCtx<K>& w, int x, int p, in
 }
 
 // Pop the vertex x at position p: clear its relation bits again.
-template <int K>
-__device__ __forceinline__ void pop_vertex(const WarpCtx<K>& w, int x, int p) {
+template <typename LT>
+__device__ __forceinline__ void pop_vertex(const WarpCtx<LT>& w, int x, int p) {
   const int rs = w.urow[x], re = w.urow[x + 1];
   const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
-  const LabT<K> clear = (LabT<K>)~(3u << (2 * p));
+  const LT clear = (LT)~(3u << (2 * p));
   for (int b = start; b < re; b += 32) {
     const int i = b + w.lane;
     if (i < re) {
@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   sp += a.hist_bytes;
   unsigned char* mine =
       sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
-  LabT<K>* lab = LS ? (LabT<K>*)mine
-                    : (LabT<K>*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.nmax;
+  using LT = LabT<K, COMB>;
+  LT* lab = LS ? (LT*)mine : (LT*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.nmax;
   uint16_t* buf = (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
   // combinatorial mode: per-cell counts (choices in the low, tail in the high
   // 16 bits), the list of non-empty cells, and its length
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   if (tid == 0) s_cur_g = (int)(((int64_t)blockIdx.x * a.G) / gridDim.x);
   __syncthreads();
 
-  WarpCtx<K> w;
+  WarpCtx<LT> w;
   w.lab = lab;
   w.buf = buf;
   w.cap = a.cap;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           const uint32_t l0 = lab[u];
           lam = l0 & LM;
           inc = i < ce;
-          lab[u] = (LabT<K>)(l0 | (inc ? INC : INT));
+          lab[u] = (LT)(l0 | (inc ? INC : INT));
           tag = lam | (inc ? 0x10000u : 0u);
         }
         const unsigned peers = __match_any_sync(kFull, tag);
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       // 4. clear flags and cells
       for (int b = c; b < e; b += 32) {
         const int i = b + lane;
-        if (i < e) lab[buf[i]] &= (LabT<K>)~(INC | INT);
+        if (i < e) lab[buf[i]] &= (LT)~(INC | INT);
       }
       for (int ia = lane; ia < r; ia += 32) ct[cl[ia]] = 0;
       __syncwarp();
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         if (i < re) {
           const uint32_t ent = w.ucol[i];
           const int u = (int)(ent & kVertexMask);
-          lab[u] |= (LabT<K>)(ent >> 30);
+          lab[u] |= (LT)(ent >> 30);
           const int q = i - f - j1a;
           if (q >= 0) {
             if (q < w.cap) buf[q] = (uint16_t)u;
@@ -569,28 +569,95 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           pair_level(c, ce, e, key);
           if (L == 1) break;
           L -= 1;
-          pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+          pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
           continue;
         }
         if (!COMB && L == K - 2) {
-          // choosing the (k-1)-th vertex: its k-sets are classified right here.
+          // Choosing the (k-1)-th vertex finishes its k-sets in place, for up
+          // to GS consecutive choices at once (as many as the relation word
+          // has free 2-bit slots: 3, 2, 1, 4 for k = 3..6): choice g marks its
+          // row into slot g above the first k-2 positions' bits, so one pass
+          // over the shared candidate tail classifies every choice's leaves.
           if (c >= ce) {
             if (L == 1) break;
             L -= 1;
-            pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+            pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
             continue;
           }
-          const int y = buf[c];
-          if (lane == L) s_c = c + 1;
-          const uint32_t P2 = key | ((uint32_t)lab[y] << (L * (L - 1)));
-          constexpr int OFF1 = (K - 1) * (K - 2);
           constexpr int NB = 2 * (K - 2);
-          // (a) y's row: mark its relation bits; an exclusive neighbour u (no
-          //     relation to the first k-2 vertices) completes a k-set whose key
-          //     is fixed by the arc code between y and u
-          {
+          constexpr uint32_t LM = (1u << NB) - 1u;
+          constexpr int OFF1 = (K - 1) * (K - 2);
+          constexpr int OFF2 = (K - 2) * (K - 3);
+          // slots left in the relation word above the first k-2 positions
+          constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 4 ? (8 * (int)sizeof(LT) - NB) / 2 : 4;
+          if constexpr (GS == 1) {
+            // one choice at a time, two batches of leaves in flight
+            const int y = buf[c];
+            if (lane == L) s_c = c + 1;
+            const uint32_t P2 = key | ((uint32_t)lab[y] << (L * (L - 1)));
+            // (a) y's row: mark its relation bits; an exclusive neighbour u (no
+            //     relation to the first k-2 vertices) completes a k-set whose key
+            //     is fixed by the arc code between y and u
+            {
+              const int rs = w.urow[y], re = w.urow[y + 1];
+              const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
+              int n1 = 0, n2 = 0, n3 = 0;
+              for (int b = start; b < re; b += 32) {
+                const int j = b + lane;
+                bool ex = false;
+                uint32_t code = 0;
+                if (j < re) {
+                  const uint32_t ent = w.ucol[j];
+                  const int u = (int)(ent & kVertexMask);
+                  code = ent >> 30;
+                  if (u > w.root) {
+                    const LT old = lab[u];
+                    lab[u] = (LT)(old | (code << NB));
+                    ex = old == 0;
+                  }
+                }
+                n1 += __popc(__ballot_sync(kFull, ex && code == 1));
+                n2 += __popc(__ballot_sync(kFull, ex && code == 2));
+                n3 += __popc(__ballot_sync(kFull, ex && code == 3));
+              }
+              __syncwarp();
+              if (lane < 3) {
+                const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
+                if (cnt) hadd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+              }
+            }
+            // (b) the tail buf[c+1, e): relation words now include y's bits
+            for (int b = c + 1; b < e; b += 64) {
+              const int i0 = b + lane, i1 = b + 32 + lane;
+              const bool v0 = i0 < e, v1 = i1 < e;
+              const uint32_t l0 = v0 ? (uint32_t)lab[buf[i0]] : 0xFFFFFFFFu;
+              const uint32_t l1 = v1 ? (uint32_t)lab[buf[i1]] : 0xFFFFFFFFu;
+              const unsigned p0 = __match_any_sync(kFull, l0);
+              const unsigned p1 = __match_any_sync(kFull, l1);
+              const bool lead0 = v0 && lane == __ffs(p0) - 1;
+              const bool lead1 = v1 && lane == __ffs(p1) - 1;
+              uint32_t id0 = kNoClass, id1 = kNoClass;
+              if (lead0) id0 = __ldg(&a.table[P2 | (l0 << OFF1)]);
+              if (lead1) id1 = __ldg(&a.table[P2 | (l1 << OFF1)]);
+              if (lead0) hadd(id0, __popc(p0));
+              if (lead1) hadd(id1, __popc(p1));
+            }
+            // (c) unmark y
+            pop_vertex(w, y, L);
+            continue;
+          }
+          const int ng = min(GS, ce - c);
+          if (lane == L) s_c = c + ng;
+          uint32_t Pg = 0;  // key prefix of choice `lane`
+          if (lane < ng) Pg = key | ((uint32_t)(lab[buf[c + lane]] & LM) << OFF2);
+          // (a) each choice's row: mark its slot; an exclusive neighbour u (no
+          //     relation to the first k-2 vertices) completes a k-set whose
+          //     key is fixed by the arc code between the choice and u
+          for (int gg = 0; gg < ng; ++gg) {
+            const int y = buf[c + gg];
             const int rs = w.urow[y], re = w.urow[y + 1];
             const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
+            const int sh = NB + 2 * gg;
             int n1 = 0, n2 = 0, n3 = 0;
             for (int b = start; b < re; b += 32) {
               const int j = b + lane;
@@ -601,9 +668,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                 const int u = (int)(ent & kVertexMask);
                 code = ent >> 30;
                 if (u > w.root) {
-                  const LabT<K> old = lab[u];
-                  lab[u] = (LabT<K>)(old | (code << NB));
-                  ex = old == 0;
+                  const LT old = lab[u];
+                  lab[u] = (LT)(old | (code << sh));
+                  ex = (old & LM) == 0;
                 }
               }
               n1 += __popc(__ballot_sync(kFull, ex && code == 1));
@@ -611,36 +678,37 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
               n3 += __popc(__ballot_sync(kFull, ex && code == 3));
             }
             __syncwarp();
+            const uint32_t pg = __shfl_sync(kFull, Pg, gg);
             if (lane < 3) {
               const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
-              if (cnt) hadd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+              if (cnt) hadd(__ldg(&a.table[pg | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
             }
           }
-          // (b) the tail buf[c+1, e): relation words now include y's bits
-          for (int b = c + 1; b < e; b += 64) {
-            const int i0 = b + lane, i1 = b + 32 + lane;
-            const bool v0 = i0 < e, v1 = i1 < e;
-            const uint32_t l0 = v0 ? (uint32_t)lab[buf[i0]] : 0xFFFFFFFFu;
-            const uint32_t l1 = v1 ? (uint32_t)lab[buf[i1]] : 0xFFFFFFFFu;
-            const unsigned p0 = __match_any_sync(kFull, l0);
-            const unsigned p1 = __match_any_sync(kFull, l1);
-            const bool lead0 = v0 && lane == __ffs(p0) - 1;
-            const bool lead1 = v1 && lane == __ffs(p1) - 1;
-            uint32_t id0 = kNoClass, id1 = kNoClass;
-            if (lead0) id0 = __ldg(&a.table[P2 | (l0 << OFF1)]);
-            if (lead1) id1 = __ldg(&a.table[P2 | (l1 << OFF1)]);
-            if (lead0) hadd(id0, __popc(p0));
-            if (lead1) hadd(id1, __popc(p1));
+          // (b) the candidates after the group's first choice; those after
+          //     choice g are its leaves, keyed by their word to the first k-2
+          //     vertices plus slot g; equal keys of a batch share a table read
+          for (int b = c + 1; b < e; b += 32) {
+            const int i0 = b + lane;
+            const bool v0 = i0 < e;
+            const uint32_t lt = v0 ? (uint32_t)lab[buf[i0]] : 0u;
+            for (int gg = 0; gg < ng; ++gg) {
+              const bool vg = v0 && i0 > c + gg;
+              const uint32_t wd = (lt & LM) | (((lt >> (NB + 2 * gg)) & 3u) << NB);
+              const uint32_t pg = __shfl_sync(kFull, Pg, gg);
+              const unsigned peers = __match_any_sync(kFull, vg ? wd : 0xFFFFFFFFu);
+              if (vg && lane == __ffs(peers) - 1)
+                hadd(__ldg(&a.table[pg | (wd << OFF1)]), __popc(peers));
+            }
           }
-          // (c) unmark y
-          pop_vertex<K>(w, y, L);
+          // (c) clear the slots
+          for (int gg = 0; gg < ng; ++gg) pop_vertex(w, buf[c + gg], L + gg);
           continue;
         }
         if (c < ce) {
           const int x = buf[c];
           if (lane == L) s_c = c + 1;
           const uint32_t nkey = key | ((uint32_t)lab[x] << (L * (L - 1)));
-          const int ne = push_vertex<K>(w, x, L, e);
+          const int ne = push_vertex(w, x, L, e);
           if (lane == L) s_vert = x;
           if (lane == L + 1) {
             s_c = c + 1;
@@ -656,13 +724,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         } else {
           if (L == 1) break;
           L -= 1;
-          pop_vertex<K>(w, __shfl_sync(kFull, s_vert, L), L);
+          pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
         }
       }
       // pop the root
       for (int b = f; b < re; b += 32) {
         const int i = b + lane;
-        if (i < re) lab[w.ucol[i] & kVertexMask] &= (LabT<K>)~3u;
+        if (i < re) lab[w.ucol[i] & kVertexMask] &= (LT)~3u;
       }
       __syncwarp();
     }
@@ -752,7 +820,8 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
   p->comb = tuning && tuning->method == MT_METHOD_CELLS;
-  const size_t lab_bytes = round16((size_t)nmax * (K <= 5 ? 1 : 2));
+  const size_t lab_elem = K <= 5 ? 1 : 2;
+  const size_t lab_bytes = round16((size_t)nmax * lab_elem);
   const size_t cells = (size_t)1 << (2 * (K - 2));
   const size_t cell_bytes =
       p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 384 + 16 : 0;
@@ -812,7 +881,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->off_cnt = off; off += round16(((size_t)G * nmax + 1) * 4);
   p->off_items = off; off += round16(p->items_max * sizeof(Item));
   p->off_lab = off;
-  if (!p->lab_smem) off += round16((size_t)p->blocks * p->warps_per_block * nmax * (K <= 5 ? 1 : 2));
+  if (!p->lab_smem) off += round16((size_t)p->blocks * p->warps_per_block * nmax * lab_elem);
   p->ws_bytes = off + 256;
   return MT_OK;
 }
@@ -863,7 +932,8 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
                                                       p.split_scale, target, p.items_factor, rb,
                                                       re);
   if (!p.lab_smem) {
-    e = cudaMemsetAsync(lab, 0, (size_t)p.blocks * p.warps_per_block * p.nmax * (K <= 5 ? 1 : 2), s);
+    e = cudaMemsetAsync(lab, 0,
+                        (size_t)p.blocks * p.warps_per_block * p.nmax * (K <= 5 ? 1 : 2), s);
     if (e != cudaSuccess) return e;
   }
   CountArgs a;
