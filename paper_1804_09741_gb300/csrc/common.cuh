@@ -10,7 +10,6 @@
 
 namespace mt {
 
-constexpr int kMaxK = 6;
 constexpr int kMaxVertices = 65535;  // vertex ids are stored as uint16 on the device stacks
 constexpr uint32_t kNoClass = 0xFFFFFFFFu;
 
@@ -20,7 +19,6 @@ constexpr uint32_t kNumClasses[7] = {0, 1, 2, 13, 199, 9364, 1530843};
 // Error bits written by kernels into a device status word.
 constexpr uint32_t kErrStackOverflow = 1u;
 constexpr uint32_t kErrDuplicateArc = 2u;
-constexpr uint32_t kErrHashFull = 4u;
 
 // Undirected neighbour entry: vertex id in bits 0..29, bit 30 set iff the arc
 // row-vertex -> neighbour exists, bit 31 set iff neighbour -> row-vertex exists

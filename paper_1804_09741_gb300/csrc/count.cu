@@ -69,16 +69,7 @@ __device__ __forceinline__ float branch_cost(int x1) {
   return 1.f + (float)x1 + choose_f(x1, K - 2) * (K >= 4 ? 2.f : 1.f);
 }
 
-// First index in sorted packed entries [lo, hi) whose vertex is > x.
-__device__ __forceinline__ int first_above(const uint32_t* __restrict__ ucol, int lo, int hi,
-                                           int x) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if ((int)(__ldg(&ucol[mid]) & kVertexMask) > x) hi = mid; else lo = mid + 1;
-  }
-  return lo;
-}
-
+// Whether vertex x is in sorted packed entries [lo, hi).
 __device__ __forceinline__ bool contains(const uint32_t* __restrict__ ucol, int lo, int hi, int x) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
