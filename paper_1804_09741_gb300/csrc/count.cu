@@ -53,6 +53,8 @@ struct Hdr {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kTargetItemsPerWarp = 64;
 constexpr int kMaxWarpsPerBlock = 32;
+// Per-warp stack of suspended DFS levels: (cursor, choice end, tail end, key, vertex).
+constexpr int kLevelBytes = 128;
 
 __device__ __forceinline__ float choose_f(int x, int r) {
   if (x < r) return 0.f;
@@ -316,7 +318,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   int32_t* s_hist = (int32_t*)sp;
   sp += a.hist_bytes;
   unsigned char* mine =
-      sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
+      sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0) +
+                          kLevelBytes);
+  int* lvs = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
   using LT = LabT<K, COMB>;
   LT* lab = LS ? (LT*)mine : (LT*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.nmax;
   uint16_t* buf = (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
@@ -541,26 +545,29 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         }
       }
       __syncwarp();
-      int s_c = 0, s_ce = 0, s_e = 0, s_vert = 0;
-      uint32_t s_key = 0;
-      if (lane == 1) {
-        s_c = 0;
-        s_e = min(dplus - j1a, w.cap);
-        s_ce = min(j1b - j1a, s_e);
-      }
-      if (lane == 0) s_vert = v;
+      // the current level's state lives in (warp-uniform) registers; the
+      // levels above it wait in the per-warp stack `lvs`
+      int cur_e = min(dplus - j1a, w.cap);
+      int cur_c = 0, cur_ce = min(j1b - j1a, cur_e);
+      uint32_t cur_key = 0;
       const bool has2 = it.b2 != 0xFFFF;
       int L = 1;
+      auto pop_level = [&]() {
+        L -= 1;
+        const int* sv = lvs + 5 * L;
+        cur_c = sv[0];
+        cur_ce = sv[1];
+        cur_e = sv[2];
+        cur_key = (uint32_t)sv[3];
+        pop_vertex(w, sv[4], L);
+      };
       while (true) {
-        const int c = __shfl_sync(kFull, s_c, L);
-        const int ce = __shfl_sync(kFull, s_ce, L);
-        const int e = __shfl_sync(kFull, s_e, L);
-        const uint32_t key = __shfl_sync(kFull, s_key, L);
+        const int c = cur_c, ce = cur_ce, e = cur_e;
+        const uint32_t key = cur_key;
         if (COMB && L == K - 2) {
           pair_level(c, ce, e, key);
           if (L == 1) break;
-          L -= 1;
-          pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
+          pop_level();
           continue;
         }
         if (!COMB && L == K - 2) {
@@ -571,8 +578,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           // over the shared candidate tail classifies every choice's leaves.
           if (c >= ce) {
             if (L == 1) break;
-            L -= 1;
-            pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
+            pop_level();
             continue;
           }
           constexpr int NB = 2 * (K - 2);
@@ -584,7 +590,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           if constexpr (GS == 1) {
             // one choice at a time, two batches of leaves in flight
             const int y = buf[c];
-            if (lane == L) s_c = c + 1;
+            cur_c = c + 1;
             const uint32_t P2 = key | ((uint32_t)lab[y] << (L * (L - 1)));
             // (a) y's row: mark its relation bits; an exclusive neighbour u (no
             //     relation to the first k-2 vertices) completes a k-set whose key
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             continue;
           }
           const int ng = min(GS, ce - c);
-          if (lane == L) s_c = c + ng;
+          cur_c = c + ng;
           uint32_t Pg = 0;  // key prefix of choice `lane`
           if (lane < ng) Pg = key | ((uint32_t)(lab[buf[c + lane]] & LM) << OFF2);
           // (a) each choice's row: mark its slot; an exclusive neighbour u (no
@@ -697,25 +703,29 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         }
         if (c < ce) {
           const int x = buf[c];
-          if (lane == L) s_c = c + 1;
           const uint32_t nkey = key | ((uint32_t)lab[x] << (L * (L - 1)));
           const int ne = push_vertex(w, x, L, e);
-          if (lane == L) s_vert = x;
-          if (lane == L + 1) {
-            s_c = c + 1;
-            s_ce = ne;
-            s_e = ne;
-            s_key = nkey;
+          if (lane == 0) {
+            int* sv = lvs + 5 * L;
+            sv[0] = c + 1;
+            sv[1] = ce;
+            sv[2] = e;
+            sv[3] = (int)key;
+            sv[4] = x;
           }
-          if (L == 1 && has2 && lane == 2) {
-            s_c = c + 1 + it.a2;
-            s_ce = min(c + 1 + (int)it.b2, ne);
+          __syncwarp();
+          cur_c = c + 1;
+          cur_ce = ne;
+          cur_e = ne;
+          cur_key = nkey;
+          if (L == 1 && has2) {
+            cur_c = c + 1 + it.a2;
+            cur_ce = min(c + 1 + (int)it.b2, ne);
           }
           L += 1;
         } else {
           if (L == 1) break;
-          L -= 1;
-          pop_vertex(w, __shfl_sync(kFull, s_vert, L), L);
+          pop_level();
         }
       }
       // pop the root
@@ -816,7 +826,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   const size_t cells = (size_t)1 << (2 * (K - 2));
   const size_t cell_bytes =
       p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 384 + 16 : 0;
-  const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes;
+  const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes + kLevelBytes;
   const size_t hist_bytes = K <= 5 ? round16((size_t)classes * 4) : 0;
   const size_t graph_bytes = round16((size_t)(nmax + 1) * 4) + round16((size_t)p->nu_cap * 4);
   int dev = 0, sms = 0, max_smem = 0;
@@ -852,7 +862,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->graph_bytes = p->gcache ? graph_bytes : 0;
   p->hist_bytes = hist_bytes;
   p->lab_bytes = lab_bytes;
-  p->buf_bytes = buf_bytes - cell_bytes;
+  p->buf_bytes = buf_bytes - cell_bytes - kLevelBytes;
   p->cell_bytes = cell_bytes;
   const void* kern = pick_kernel(K, p->gcache, p->lab_smem, p->comb);
   MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
