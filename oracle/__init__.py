@@ -79,6 +79,9 @@ def _load():
             lib.oracle_count_bruteforce.restype = ctypes.c_int64
             lib.oracle_count_bruteforce.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int,
                                                     u32p, u64p, ctypes.c_int64, u64p]
+            lib.oracle_randomize_dyads.restype = ctypes.c_int64
+            lib.oracle_randomize_dyads.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_uint64,
+                                                   ctypes.c_uint64, i32p, i32p]
             lib.oracle_randomize.restype = ctypes.c_int64
             lib.oracle_randomize.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_uint64,
                                              ctypes.c_uint64, i32p, i32p]
@@ -192,6 +195,17 @@ def randomize(g, seed: int, swaps: int):
     col_out = np.empty(max(g.m, 1), np.int32)
     acc = _load().oracle_randomize(g.n, _p(rp, ctypes.c_int32), _p(col, ctypes.c_int32), seed,
                                    swaps, _p(rp_out, ctypes.c_int32), _p(col_out, ctypes.c_int32))
+    return rp_out, col_out[:g.m].copy(), int(acc)
+
+
+def randomize_dyads(g, seed: int, attempts: int):
+    """Dyad-preserving null graph: returns (row_ptr, col, accepted swaps)."""
+    rp, col = _csr(g)
+    rp_out = np.empty(g.n + 1, np.int32)
+    col_out = np.empty(max(g.m, 1), np.int32)
+    acc = _load().oracle_randomize_dyads(g.n, _p(rp, ctypes.c_int32), _p(col, ctypes.c_int32),
+                                         seed, attempts, _p(rp_out, ctypes.c_int32),
+                                         _p(col_out, ctypes.c_int32))
     return rp_out, col_out[:g.m].copy(), int(acc)
 
 

@@ -415,4 +415,74 @@ int64_t oracle_randomize(int32_t n, const int32_t* row_ptr, const int32_t* col, 
   return accepted;
 }
 
+// Dyad-preserving randomiser (reading of the "swap mutual pairs and one-way
+// arcs separately" null model): the single arcs (u->v without v->u) and the
+// mutual dyads {u,v} are two lists in CSR order (a dyad listed once, from its
+// smaller end).  Attempt t takes SplitMix64 outputs 3t, 3t+1, 3t+2 of the seed:
+// the first picks the kind (single if floor(r*(S+D)/2^64) < S, else dyad), the
+// other two pick two entries of that list (index = floor(r*len/2^64)).
+//  * singles (a->b), (c->d) become (a->d), (c->b);
+//  * dyads {a,b}, {c,d} become {a,d}, {c,b};
+// rejected (and counted as used) if the two entries coincide, a == c, b == d,
+// a == d, c == b, or a new pair is already adjacent in either direction.
+// In- and out-degrees, the number of mutual dyads per vertex and the dyad
+// census are preserved.  The CSR is rebuilt by sorting at the end.
+int64_t oracle_randomize_dyads(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                               uint64_t seed, uint64_t attempts, int32_t* row_ptr_out,
+                               int32_t* col_out) {
+  std::set<std::pair<int, int>> arcs_in;
+  for (int v = 0; v < n; ++v)
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) arcs_in.insert({v, col[e]});
+  std::vector<std::pair<int, int>> singles, dyads;
+  for (int v = 0; v < n; ++v)
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      const int u = col[e];
+      if (arcs_in.count({u, v})) {
+        if (v < u) dyads.emplace_back(v, u);
+      } else {
+        singles.emplace_back(v, u);
+      }
+    }
+  // adjacency of unordered pairs
+  std::set<std::pair<int, int>> adj;
+  for (auto& a : arcs_in) adj.insert({std::min(a.first, a.second), std::max(a.first, a.second)});
+  auto key = [](int x, int y) { return std::make_pair(std::min(x, y), std::max(x, y)); };
+  const uint64_t S = singles.size(), D = dyads.size();
+  int64_t accepted = 0;
+  for (uint64_t t = 0; t < attempts && S + D > 0; ++t) {
+    const uint64_t r0 = splitmix64_output(seed, 3 * t);
+    const uint64_t r1 = splitmix64_output(seed, 3 * t + 1);
+    const uint64_t r2 = splitmix64_output(seed, 3 * t + 2);
+    const uint64_t pick = (uint64_t)(((unsigned __int128)r0 * (unsigned __int128)(S + D)) >> 64);
+    const bool single = pick < S;
+    std::vector<std::pair<int, int>>& L = single ? singles : dyads;
+    const uint64_t len = L.size();
+    const uint64_t e1 = (uint64_t)(((unsigned __int128)r1 * (unsigned __int128)len) >> 64);
+    const uint64_t e2 = (uint64_t)(((unsigned __int128)r2 * (unsigned __int128)len) >> 64);
+    if (e1 == e2) continue;
+    const int a = L[e1].first, b = L[e1].second, c = L[e2].first, d = L[e2].second;
+    if (a == c || b == d || a == d || c == b) continue;
+    if (adj.count(key(a, d)) || adj.count(key(c, b))) continue;
+    adj.erase(key(a, b));
+    adj.erase(key(c, d));
+    adj.insert(key(a, d));
+    adj.insert(key(c, b));
+    L[e1] = {a, d};
+    L[e2] = {c, b};
+    ++accepted;
+  }
+  std::vector<std::pair<int, int>> arcs(singles.begin(), singles.end());
+  for (auto& p : dyads) {
+    arcs.emplace_back(p.first, p.second);
+    arcs.emplace_back(p.second, p.first);
+  }
+  std::sort(arcs.begin(), arcs.end());
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (auto& a : arcs) cnt[a.first + 1]++;
+  row_ptr_out[0] = 0;
+  for (int v = 0; v < n; ++v) row_ptr_out[v + 1] = (int32_t)(row_ptr_out[v] + cnt[v + 1]);
+  for (size_t i = 0; i < arcs.size(); ++i) col_out[i] = arcs[i].second;
+  return accepted;
+}
+
 }  // extern "C"

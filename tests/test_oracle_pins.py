@@ -303,3 +303,52 @@ def test_zscores_closed_form_and_numpy():
     ref = (h0.astype(np.float64) - nulls.astype(np.float64).mean(0)) / nulls.astype(
         np.float64).std(0, ddof=0)
     np.testing.assert_allclose(z, ref, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ dyad-preserving randomiser
+
+
+def _dyad_census(rp, col, n):
+    src = np.repeat(np.arange(n), np.diff(rp))
+    arcs = set(zip(src.tolist(), col.tolist()))
+    mutual = {(a, b) for a, b in arcs if (b, a) in arcs and a < b}
+    mdeg = np.zeros(n, int)
+    for a, b in mutual:
+        mdeg[a] += 1
+        mdeg[b] += 1
+    return len(mutual), len(arcs) - 2 * len(mutual), mdeg
+
+
+def test_randomize_dyads_hand_worked_swap():
+    # Two mutual dyads {0,1}, {2,3}: an attempt whose two picks differ (index =
+    # top bit of outputs 1 and 2 of the seed, the kind pick is always "dyad")
+    # turns them into {0,3}, {1,2}; equal picks leave the graph alone.
+    g = syn.csr_from_arcs(4, [0, 1, 2, 3], [1, 0, 3, 2])
+    for seed in range(40):
+        i1 = oracle.splitmix64(seed, 1) >> 63
+        i2 = oracle.splitmix64(seed, 2) >> 63
+        rp, col, acc = oracle.randomize_dyads(g, seed, 1)
+        if i1 != i2:
+            assert acc == 1 and rp.tolist() == [0, 1, 2, 3, 4] and col.tolist() == [3, 2, 1, 0]
+        else:
+            assert acc == 0 and col.tolist() == [1, 0, 3, 2]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_randomize_dyads_invariants(seed):
+    g = syn.chung_lu_digraph(300, 1200, 2.2, None, 0.3, 0)
+    rp, col, acc = oracle.randomize_dyads(g, seed, 10 * g.m)
+    assert acc > g.m // 2
+    assert np.array_equal(rp, g.row_ptr)  # out-degrees
+    assert np.array_equal(np.bincount(col, minlength=g.n), np.bincount(g.col, minlength=g.n))
+    src = np.repeat(np.arange(g.n), np.diff(rp))
+    assert not np.any(src == col) and len(set(zip(src.tolist(), col.tolist()))) == g.m
+    m0, s0, d0 = _dyad_census(g.row_ptr, g.col, g.n)
+    m1, s1, d1 = _dyad_census(rp, col, g.n)
+    assert (m0, s0) == (m1, s1) and np.array_equal(d0, d1)  # reciprocity kept
+    assert not np.array_equal(col, g.col)
+    rp2, col2, acc2 = oracle.randomize_dyads(g, seed, 10 * g.m)
+    assert acc2 == acc and np.array_equal(col2, col)
+    # the plain arc swap does not keep the dyad census
+    _, colp, _ = oracle.randomize(g, seed, 10 * g.m)
+    assert _dyad_census(rp, colp, g.n)[0] != m0
