@@ -328,6 +328,10 @@ def run_ours(args, world, rank, local):
         extra["plain_vs_batched"] = measure_plain_vs_batched(
             mt, torch, dg, table, g, (1 + R) / (total_ms / args.steps / 1000.0))
         extra["k6_batch"] = measure_k6(mt, torch)
+        dyad = measure_batch_method(mt, torch, "nullmodel_k5", table, method=0, null_model=1)
+        dyad["metric"] = "k-subgraphs classified/s"
+        dyad["note"] = "same k=5 batch with the dyad-preserving null model (reciprocity kept)"
+        extra["dyad_null_model"] = dyad
         extra["cells_method"] = {
             "k5_batch": measure_batch_method(mt, torch, "nullmodel_k5", table),
             "k6_batch": measure_batch_method(mt, torch, "nullmodel_k6", None),
@@ -404,15 +408,15 @@ def _autotuned(mt, dg, t, g, method):
     return mt.make_tuning(0.0, tp.warps_per_block, tp.split_scale, tp.stack_cap, method)
 
 
-def measure_batch_method(mt, torch, name, table, method=1, steps=3, warmup=3):
-    """A null-model batch counted with another counting method."""
+def measure_batch_method(mt, torch, name, table, method=1, steps=3, warmup=3, null_model=0):
+    """A null-model batch counted with another counting method or null model."""
     w = syn.WORKLOADS[name]
     g = syn.workload_graph(name)
     own = table is None
     t = mt.table_build(w["k"]) if own else table
     dg = mt.graph_from(g)
     R = w["nulls"]
-    b = mt.Batch(dg, t, R, 10 * g.m, _autotuned(mt, dg, t, g, method))
+    b = mt.Batch(dg, t, R, 10 * g.m, _autotuned(mt, dg, t, g, method), null_model=null_model)
     seeds = np.arange(1, R + 1, dtype=np.uint64)
     hists = torch.empty((R + 1, t.num_classes), dtype=torch.int64, device="cuda")
     z = torch.empty(t.num_classes, dtype=torch.float64, device="cuda")

@@ -243,6 +243,21 @@ mt_status mt_count_stats(const mt_graph* g, uint64_t* items, uint32_t* err, floa
 mt_status mt_randomize(const mt_graph* src, uint64_t seed, uint64_t swaps, void* stream,
                        mt_graph** out);
 
+/* Dyad-preserving null graph (reciprocity kept; the paper names no model, this
+ * is the reading that swaps mutual pairs and one-way arcs separately): the arcs
+ * are split, in CSR order, into singles (u->v without v->u) and mutual dyads
+ * {u,v} listed once from the smaller end.  Attempt t = 0..attempts-1 takes
+ * SplitMix64 outputs 3t, 3t+1, 3t+2 of `seed`: the first picks the list
+ * (singles if floor(r * (S + D) / 2^64) < S), the other two pick two entries
+ * (a,b), (c,d) of it (index = floor(r * len / 2^64)), which become (a,d), (c,b)
+ * unless the entries coincide, a == c, b == d, a == d, c == b, or a new pair is
+ * already adjacent in either direction.  In- and out-degrees, each vertex's
+ * number of mutual partners and the dyad census are preserved.  Synchronises
+ * `stream`.  Errors: MT_EINVAL, MT_EUNSUPPORTED (graph too large for the
+ * on-chip arc set, m above about 17,000), MT_ENOMEM, MT_ECUDA. */
+mt_status mt_randomize_dyads(const mt_graph* src, uint64_t seed, uint64_t attempts, void* stream,
+                             mt_graph** out);
+
 /* Batched null model: the original graph plus R null graphs (seeds[r], `swaps`
  * attempts each) counted in one persistent launch.  The handle pre-allocates
  * every buffer; the first mt_batch_run captures the whole step (randomise,
@@ -255,6 +270,17 @@ mt_status mt_batch_free(mt_batch* b);
 /* mt_batch_create with explicit tuning of the counting launch (NULL = automatic). */
 mt_status mt_batch_create_tuned(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
                                 const mt_tuning* tuning, mt_batch** out);
+
+/* Null models of a batch: degree-preserving arc swaps (mt_randomize) or
+ * dyad-preserving swaps that also keep reciprocity (mt_randomize_dyads). */
+typedef enum { MT_NULL_ARC_SWAP = 0, MT_NULL_DYAD_SWAP = 1 } mt_null_model;
+
+/* mt_batch_create with a choice of null model (an mt_null_model) and tuning
+ * (NULL = automatic).  `swaps` is the number of attempts per null graph.
+ * Errors: as mt_batch_create, MT_EUNSUPPORTED for a dyad model on a graph too
+ * large for its on-chip arc set. */
+mt_status mt_batch_create_ex(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
+                             int null_model, const mt_tuning* tuning, mt_batch** out);
 
 /* Run a batch.  `seeds`: HOST array of R uint64.  `hists`: uint64[(R+1)*C]
  * (row 0 = original graph, row r = null graph r), device or host.  `z`:

@@ -37,6 +37,7 @@ class Tuning(ctypes.Structure):
 
 
 METHOD_ENUMERATE, METHOD_CELLS = 0, 1
+NULL_ARC_SWAP, NULL_DYAD_SWAP = 0, 1
 
 
 # Every entry point of include/motifs.h with its ctypes signature.
@@ -62,8 +63,11 @@ SIGNATURES = {
     "mt_count_stats": (ctypes.c_int, [_vp, _P(_u64), _P(_u32), _P(ctypes.c_float)]),
     "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_randomize": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
+    "mt_randomize_dyads": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_batch_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(_vp)]),
     "mt_batch_create_tuned": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(Tuning), _P(_vp)]),
+    "mt_batch_create_ex": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, ctypes.c_int, _P(Tuning),
+                                          _P(_vp)]),
     "mt_batch_free": (ctypes.c_int, [_vp]),
     "mt_batch_run": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "mt_batch_phase_ms": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
@@ -314,13 +318,26 @@ def randomize(g: Graph, seed: int, swaps: int, stream=None) -> Graph:
     return Graph(h.value)
 
 
+def randomize_dyads(g: Graph, seed: int, attempts: int, stream=None) -> Graph:
+    """Null graph that keeps reciprocity (mt_randomize_dyads)."""
+    h = _vp()
+    _check(_lib.mt_randomize_dyads(g.handle, seed, attempts, _stream(stream), ctypes.byref(h)),
+           "mt_randomize_dyads")
+    return Graph(h.value)
+
+
 class Batch:
     """The original graph plus R null graphs counted in one captured step."""
 
-    def __init__(self, g: Graph, t: Table, R: int, swaps: int, tuning: Tuning | None = None):
+    def __init__(self, g: Graph, t: Table, R: int, swaps: int, tuning: Tuning | None = None,
+                 null_model: int = 0):
         self.g, self.t, self.R, self.swaps = g, t, R, swaps
         h = _vp()
-        if tuning is None:
+        if null_model:
+            _check(_lib.mt_batch_create_ex(g.handle, t.handle, R, swaps, int(null_model),
+                                           ctypes.byref(tuning) if tuning is not None else None,
+                                           ctypes.byref(h)), "mt_batch_create_ex")
+        elif tuning is None:
             _check(_lib.mt_batch_create(g.handle, t.handle, R, swaps, ctypes.byref(h)),
                    "mt_batch_create")
         else:

@@ -18,6 +18,12 @@ cudaError_t launch_randomize(int32_t n, int32_t m, int G, const int32_t* row_ptr
                              int32_t* col_out, uint32_t* gscratch, int64_t* accepted,
                              cudaStream_t s);
 size_t rand_gscratch_words(int32_t m, int G);
+cudaError_t launch_randomize_dyads(int32_t n, int32_t m, int G, const int32_t* row_ptr,
+                                   const int32_t* col0, const uint64_t* seeds, uint64_t attempts,
+                                   int32_t* col_out, int32_t* scratch, int64_t* accepted,
+                                   cudaStream_t s);
+size_t dyad_scratch_ints(int32_t n, int32_t m);
+size_t rand_smem_bytes(int32_t m);
 }  // namespace mt
 
 struct mt_batch {
@@ -37,6 +43,8 @@ struct mt_batch {
   int32_t *in_ptr = nullptr, *in_tmp = nullptr, *in_col = nullptr, *cursor = nullptr;
   mt::BuildStats* stats = nullptr;
   uint32_t* rand_scratch = nullptr;
+  int null_model = MT_NULL_ARC_SWAP;
+  int32_t* dyad_scratch = nullptr;
   uint64_t* d_seeds = nullptr;
   mt::DevGraph* d_graphs = nullptr;
   unsigned long long* d_hists = nullptr;
@@ -86,7 +94,7 @@ __global__ void k_zscore(const unsigned long long* hists, int R, uint32_t C, dou
 static size_t r16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint64_t swaps,
-                              const mt_tuning* tuning, mt_batch** out) {
+                              int null_model, const mt_tuning* tuning, mt_batch** out) {
   const int K = table_k(t);
   const uint32_t C = table_classes(t);
   const int32_t n = g0->n, m = g0->m;
@@ -102,6 +110,7 @@ static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint
 
   mt_batch* b = new mt_batch();
   b->g0 = g0; b->t = t; b->R = R; b->swaps = swaps; b->K = K; b->C = C; b->n = n; b->m = m;
+  b->null_model = null_model;
   mt_status st = count_configure_tuned(&b->plan, K, R + 1, n, dbound,
                                        (int64_t)(R + 1) * std::max(m, 1),
                                        2 * (int64_t)std::max(m, 1), C, tuning);
@@ -129,6 +138,8 @@ static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint
   const size_t o_cursor = take((size_t)R * n * 4);
   const size_t o_stats = take((size_t)R * sizeof(BuildStats));
   const size_t o_rs = take(rs_words * 4);
+  const size_t o_ds =
+      take(null_model == MT_NULL_DYAD_SWAP ? (size_t)R * dyad_scratch_ints(n, m) * 4 : 0);
   const size_t o_seeds = take((size_t)R * 8);
   const size_t o_graphs = take((size_t)(R + 1) * sizeof(DevGraph));
   const size_t o_hists = take((size_t)(R + 1) * C * 8);
@@ -154,6 +165,7 @@ static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint
   b->cursor = (int32_t*)(base + o_cursor);
   b->stats = (BuildStats*)(base + o_stats);
   b->rand_scratch = rs_words ? (uint32_t*)(base + o_rs) : nullptr;
+  b->dyad_scratch = null_model == MT_NULL_DYAD_SWAP ? (int32_t*)(base + o_ds) : nullptr;
   b->d_seeds = (uint64_t*)(base + o_seeds);
   b->d_graphs = (DevGraph*)(base + o_graphs);
   b->d_hists = (unsigned long long*)(base + o_hists);
@@ -203,8 +215,12 @@ static mt_status batch_enqueue(mt_batch* b, cudaStream_t s) {
   const size_t m1 = (size_t)std::max(m, 1);
   MT_CUDA_TRY(cudaMemcpyAsync(b->d_seeds, b->h_seeds, (size_t)R * 8, cudaMemcpyHostToDevice, s));
   MT_CUDA_TRY(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal));
-  MT_CUDA_TRY(launch_randomize(n, m, R, b->g0->row_ptr, b->g0->col, b->d_seeds, b->swaps,
-                               b->col_rand, b->rand_scratch, nullptr, s));
+  if (b->null_model == MT_NULL_DYAD_SWAP)
+    MT_CUDA_TRY(launch_randomize_dyads(n, m, R, b->g0->row_ptr, b->g0->col, b->d_seeds, b->swaps,
+                                       b->col_rand, b->dyad_scratch, nullptr, s));
+  else
+    MT_CUDA_TRY(launch_randomize(n, m, R, b->g0->row_ptr, b->g0->col, b->d_seeds, b->swaps,
+                                 b->col_rand, b->rand_scratch, nullptr, s));
   BuildArgs a;
   a.n = n; a.m = m; a.G = R;
   a.row_ptr = b->g0->row_ptr; a.row_stride = 0;
@@ -280,7 +296,20 @@ extern "C" {
 mt_status mt_batch_create(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
                           mt_batch** out) {
   if (!g || !t || !out || R < 1) return MT_EINVAL;
-  return batch_create(g, t, R, swaps, nullptr, out);
+  return batch_create(g, t, R, swaps, MT_NULL_ARC_SWAP, nullptr, out);
+}
+
+mt_status mt_batch_create_ex(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
+                             int null_model, const mt_tuning* tuning, mt_batch** out) {
+  if (!g || !t || !out || R < 1) return MT_EINVAL;
+  if (null_model != MT_NULL_ARC_SWAP && null_model != MT_NULL_DYAD_SWAP) return MT_EINVAL;
+  if (tuning && (tuning->split_cost < 0 || tuning->split_scale < 0 ||
+                 tuning->warps_per_block < 0 || tuning->warps_per_block > 32 ||
+                 tuning->stack_cap < 0 || tuning->stack_cap > 65535 ||
+                 tuning->method < 0 || tuning->method > 1))
+    return MT_EINVAL;
+  if (null_model == MT_NULL_DYAD_SWAP && rand_smem_bytes(g->m) > 200 * 1024) return MT_EUNSUPPORTED;
+  return batch_create(g, t, R, swaps, null_model, tuning, out);
 }
 
 mt_status mt_batch_create_tuned(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
@@ -291,7 +320,7 @@ mt_status mt_batch_create_tuned(const mt_graph* g, const mt_table* t, int R, uin
                  tuning->stack_cap < 0 || tuning->stack_cap > 65535 ||
                  tuning->method < 0 || tuning->method > 1))
     return MT_EINVAL;
-  return batch_create(g, t, R, swaps, tuning, out);
+  return batch_create(g, t, R, swaps, MT_NULL_ARC_SWAP, tuning, out);
 }
 
 mt_status mt_batch_free(mt_batch* b) {

@@ -235,6 +235,34 @@ def test_randomize_small_edge_cases(lib):
         np.testing.assert_array_equal(col, ocol)
 
 
+@pytest.mark.parametrize("name,seeds", [("nullmodel_k5", [1, 2]), ("nullmodel_k6", [3]),
+                                        ("chunglu_k4", [4])])
+def test_randomize_dyads_bit_exact(lib, name, seeds):
+    g = syn.workload_graph(name)
+    dg = lib.graph_from(g)
+    for s in seeds:
+        r = lib.randomize_dyads(dg, s, 10 * g.m)
+        rp, col = r.copy_csr()
+        orp, ocol, acc = oracle.randomize_dyads(g, s, 10 * g.m)
+        np.testing.assert_array_equal(rp, orp)
+        np.testing.assert_array_equal(col, ocol)
+        assert acc > 0
+
+
+def test_randomize_dyads_small_cases(lib):
+    for g, att in [(syn.csr_from_arcs(4, [0, 1, 2, 3], [1, 0, 3, 2]), 1),
+                   (syn.complete_digraph(5), 40), (syn.empty_graph(3), 5),
+                   (syn.random_small_digraph(40, 0.15, 0.5, 9), 0),
+                   (syn.random_small_digraph(40, 0.15, 0.5, 9), 2000),
+                   (syn.directed_cycle(9), 300)]:
+        for seed in (0, 5):
+            r = lib.randomize_dyads(lib.graph_from(g), seed, att)
+            rp, col = r.copy_csr()
+            orp, ocol, _ = oracle.randomize_dyads(g, seed, att)
+            np.testing.assert_array_equal(rp, orp)
+            np.testing.assert_array_equal(col, ocol)
+
+
 def test_duplicate_arc_rejected_on_device(lib):
     with pytest.raises(lib.MotifsError) as ei:
         lib.graph_load_csr(3, [0, 2, 2, 2], [1, 1])
@@ -302,3 +330,26 @@ def test_batch_full_size_k5(lib, tables):
             want, _ = oracle.count_roots(gr, 5, np.arange(500, 530))
             np.testing.assert_array_equal(lib.count_roots(nul, t, 500, 530), oracle_dense(want, cm))
     np.testing.assert_array_equal(z, oracle.zscores(hists[0], hists[1:]))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_batch_dyad_null_model(lib, tables, method):
+    """The batch with the dyad-preserving null model: rows equal the oracle's
+    counts of the oracle's dyad-preserving null graphs; z from its formula."""
+    g = syn.chung_lu_digraph(150, 500, 2.3, None, 0.3, 21)
+    t = tables(4)
+    dg = lib.graph_from(g)
+    R = 5
+    seeds = np.arange(1, R + 1, dtype=np.uint64)
+    tun = lib.make_tuning(method=method) if method else None
+    b = lib.Batch(dg, t, R, 10 * g.m, tun, null_model=lib.NULL_DYAD_SWAP)
+    hists, z = b.run(seeds)
+    hists = lib.to_numpy_u64(hists)
+    assert b.error() == 0
+    cm = t.class_masks()
+    for r in range(R):
+        rp, col, _ = oracle.randomize_dyads(g, int(seeds[r]), 10 * g.m)
+        np.testing.assert_array_equal(hists[r + 1],
+                                      oracle_dense(oracle.count(syn.Graph(g.n, rp, col), 4)[0], cm))
+    np.testing.assert_array_equal(z.cpu().numpy(), oracle.zscores(hists[0], hists[1:]))
+
