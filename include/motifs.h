@@ -23,7 +23,9 @@
  *   in by the caller stay the caller's.  Pointers documented as "device or host"
  *   are inspected with cudaPointerGetAttributes: a device pointer keeps the call
  *   asynchronous, a host pointer makes the call copy and synchronise the stream.
- * - A handle may be used by one host thread at a time.
+ * - A handle may be used by one host thread at a time.  Counting calls on one
+ *   graph handle share its scratch memory: order them on one stream (or
+ *   synchronise between them).
  * - Graphs: n vertices numbered 0..n-1 (1 <= n <= 65535), m arcs given as an
  *   int32 CSR of out-neighbours (row_ptr[n+1], col[m]); rows may be unsorted;
  *   self-loops, duplicate arcs, ids outside [0,n) and non-monotone row_ptr are

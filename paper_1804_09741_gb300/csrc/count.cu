@@ -992,7 +992,8 @@ static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist
   const size_t need = p.ws_bytes + extra;
   if (g->ws_bytes < need) {
     if (g->ws) {
-      MT_CUDA_TRY(cudaStreamSynchronize(s));
+      // an earlier count may still use the old scratch, on any stream
+      MT_CUDA_TRY(cudaDeviceSynchronize());
       cudaFree(g->ws);
       g->ws = nullptr;
       g->ws_bytes = 0;
