@@ -340,6 +340,19 @@ def run_ours(args, world, rank, local):
         extra["serving"] = measure_serving(mt, torch, {5: table})
         extra["serving_cells"] = measure_serving(mt, torch, {5: table}, method=1)
 
+    gar = None
+    if rank == 0 and R and count_ms:
+        # ceilings of one random table read and one random histogram add per
+        # subgraph (k=5 table: 2^20 words; a histogram of 9,364 -> 2^14 counters)
+        gps, aps = mt.probe_rates(1 << 20, 1 << 14)
+        sub_rate = subgraphs_per_step / (statistics.mean(count_ms) / 1000.0)
+        gar = {"gather_peak_per_s": gps, "atomic_peak_per_s": aps,
+               "kernel_subgraphs_per_s": sub_rate, "frac_of_gather": sub_rate / gps,
+               "frac_of_atomic": sub_rate / aps,
+               "note": "per-subgraph ceilings: one random 4 B read from a 4 MB table and one "
+                       "random 64-bit atomic add per classified subgraph (mt_probe_rates, "
+                       "measured in this run); grouping equal keys lets the kernel exceed them"}
+
     if rank == 0:
         line = {"metric": "k-subgraphs classified/s", "value": value, "unit": "subgraphs/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -353,6 +366,7 @@ def run_ours(args, world, rank, local):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk}
         line["config"]["tuning"] = tuned or "automatic"
+        line["gather_atomic_roofline"] = gar
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:

@@ -306,6 +306,17 @@ mt_status mt_batch_error(const mt_batch* b, uint32_t* err);
 mt_status mt_count_batch(const mt_graph* g, const mt_table* t, const uint64_t* seeds, int R,
                          uint64_t swaps, uint64_t* hists, double* z, void* stream);
 
+/* ----------------------------------------------------------------- ceilings */
+
+/* Measured ceilings of the two memory operations the classification performs
+ * per subgraph: random 4-byte reads from a table of `table_words` uint32 (one
+ * table read, Sec. 3.2) and random 64-bit atomic adds into `hist_words`
+ * counters (one histogram add), both with hashed in-kernel indices and the
+ * whole GPU busy.  Sizes are powers of two.  Synchronous; allocates and frees
+ * its buffers.  Errors: MT_EINVAL, MT_ENOMEM, MT_ECUDA. */
+mt_status mt_probe_rates(uint64_t table_words, uint64_t hist_words, double* gathers_per_s,
+                         double* atomics_per_s);
+
 /* ----------------------------------------------------------------- serving */
 
 /* A request server with continuous batching (the paper has no serving layer;

@@ -73,6 +73,7 @@ SIGNATURES = {
     "mt_batch_phase_ms": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "mt_batch_error": (ctypes.c_int, [_vp, _P(_u32)]),
     "mt_count_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _u64, _vp, _vp, _vp]),
+    "mt_probe_rates": (ctypes.c_int, [_u64, _u64, _P(_f64), _P(_f64)]),
     "mt_server_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int, _f64,
                                         _P(_vp)]),
     "mt_server_free": (ctypes.c_int, [_vp]),
@@ -294,6 +295,15 @@ def count_stats(g: Graph):
     items, err, ms = _u64(), _u32(), ctypes.c_float()
     _check(_lib.mt_count_stats(g.handle, items, err, ms), "mt_count_stats")
     return int(items.value), int(err.value), float(ms.value)
+
+
+def probe_rates(table_words: int = 1 << 20, hist_words: int = 1 << 14):
+    """(random table reads/s, random 64-bit atomic adds/s) measured on the GPU."""
+    load_library()
+    g, a = _f64(), _f64()
+    _check(_lib.mt_probe_rates(table_words, hist_words, ctypes.byref(g), ctypes.byref(a)),
+           "mt_probe_rates")
+    return g.value, a.value
 
 
 def to_numpy_u64(t) -> np.ndarray:

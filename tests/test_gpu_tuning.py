@@ -85,3 +85,11 @@ def test_batch_autotuner_keeps_histograms(t5, tmp_path):
     h0, _ = mt.Batch(dg, t5, 4, 10 * g.m).run(seeds)
     h1, _ = mt.Batch(dg, t5, 4, 10 * g.m, p.tuning()).run(seeds)
     np.testing.assert_array_equal(mt.to_numpy_u64(h0), mt.to_numpy_u64(h1))
+
+
+def test_probe_rates_are_measured():
+    import paper_1804_09741_gb300 as mt
+    g, a = mt.probe_rates(1 << 20, 1 << 14)
+    assert 1e9 < g < 1e14 and 1e8 < a < 1e14
+    with pytest.raises(mt.MotifsError):
+        mt.probe_rates(1000, 1 << 14)  # not a power of two
