@@ -124,6 +124,10 @@ __global__ void __launch_bounds__(256) k_plan_est(const DevGraph* __restrict__ g
 }
 
 // Walk one root's forward branches and cut them into items (count or write).
+// One warp per root: the lanes load 32 entries at a time, every lane walks them
+// in order with the same (warp-uniform) packing state, and the many level-2
+// ranges of a split branch are written by all lanes at once, so a hub root's
+// thousands of items cost a few stores per lane instead of a serial loop.
 template <int K, bool WRITE>
 __global__ void __launch_bounds__(256) k_plan_items(const DevGraph* __restrict__ graphs,
                                                     int64_t stride, const float* est,
@@ -133,13 +137,14 @@ __global__ void __launch_bounds__(256) k_plan_items(const DevGraph* __restrict__
                                                     double target_items, double items_factor,
                                                     int root_begin, int root_end) {
   const int g = blockIdx.y;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!WRITE && g == 0 && v == 0) cnt[(int64_t)gridDim.y * nmax] = 0;
+  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+  if (!WRITE && g == 0 && v == 0 && lane == 0) cnt[(int64_t)gridDim.y * nmax] = 0;
   if (v >= nmax) return;
   const int64_t slot = (int64_t)g * nmax + v;
   const DevGraph G = graphs[g];
   if (v >= G.n || v < root_begin || v >= root_end || v < G.root_begin || v >= G.root_end) {
-    if (!WRITE) cnt[slot] = 0;
+    if (!WRITE && lane == 0) cnt[slot] = 0;
     return;
   }
   // root-split threshold: explicit, or the automatic one scaled; never so small
@@ -155,49 +160,64 @@ __global__ void __launch_bounds__(256) k_plan_items(const DevGraph* __restrict__
   const int dplus = re - f;
   int64_t pos = WRITE ? cnt[slot] : 0;
   int count = 0;
-  auto emit = [&](int j1a, int j1b, int a2, int b2) {
-    if (WRITE) {
-      if ((uint64_t)pos < items_max) {
-        Item it;
-        it.g = (uint32_t)g;
-        it.root = (uint32_t)v;
-        it.j1a = (uint16_t)j1a;
-        it.j1b = (uint16_t)j1b;
-        it.a2 = (uint16_t)a2;
-        it.b2 = (uint16_t)b2;
-        items[pos] = it;
-      } else {
-        atomicOr(&hdr->err, kErrStackOverflow);
-      }
-      ++pos;
+  auto put = [&](int64_t at, int j1a, int j1b, int a2, int b2) {
+    if ((uint64_t)at < items_max) {
+      Item it;
+      it.g = (uint32_t)g;
+      it.root = (uint32_t)v;
+      it.j1a = (uint16_t)j1a;
+      it.j1b = (uint16_t)j1b;
+      it.a2 = (uint16_t)a2;
+      it.b2 = (uint16_t)b2;
+      items[at] = it;
+    } else {
+      atomicOr(&hdr->err, kErrStackOverflow);
     }
+  };
+  auto emit = [&](int j1a, int j1b) {  // one whole-range item, written by lane 0
+    if (WRITE && lane == 0) put(pos, j1a, j1b, 0, 0xFFFF);
+    ++pos;
     ++count;
   };
   float acc = 0.f;
   int start = 0;
-  for (int j = 0; j < dplus; ++j) {
-    const int64_t e = (int64_t)g * stride + f + j;
-    const float c = est[e];
-    const int x = x1s[e];
-    if (K >= 4 && c > 2.f * Tf && x >= 2) {
-      if (j > start) emit(start, j, 0, 0xFFFF);
-      int nch = (int)ceilf(c / Tf);
-      if (nch > x) nch = x;
-      const int r2 = (x + nch - 1) / nch;
-      for (int a = 0; a < x; a += r2) emit(j, j + 1, a, min(a + r2, x));
-      start = j + 1;
-      acc = 0.f;
-    } else {
-      acc += c;
-      if (acc >= Tf) {
-        emit(start, j + 1, 0, 0xFFFF);
+  for (int base = 0; base < dplus; base += 32) {
+    float c_l = 0.f;
+    int x_l = 0;
+    if (base + lane < dplus) {
+      const int64_t e = (int64_t)g * stride + f + base + lane;
+      c_l = est[e];
+      x_l = x1s[e];
+    }
+    const int n = min(32, dplus - base);
+    for (int i = 0; i < n; ++i) {
+      const float c = __shfl_sync(kFull, c_l, i);
+      const int x = __shfl_sync(kFull, x_l, i);
+      const int j = base + i;
+      if (K >= 4 && c > 2.f * Tf && x >= 2) {
+        if (j > start) emit(start, j);
+        int nch = (int)ceilf(c / Tf);
+        if (nch > x) nch = x;
+        const int r2 = (x + nch - 1) / nch;
+        const int ns = (x + r2 - 1) / r2;
+        if (WRITE)
+          for (int t = lane; t < ns; t += 32) put(pos + t, j, j + 1, t * r2, min(t * r2 + r2, x));
+        pos += ns;
+        count += ns;
         start = j + 1;
         acc = 0.f;
+      } else {
+        acc += c;
+        if (acc >= Tf) {
+          emit(start, j + 1);
+          start = j + 1;
+          acc = 0.f;
+        }
       }
     }
   }
-  if (start < dplus) emit(start, dplus, 0, 0xFFFF);
-  if (!WRITE) cnt[slot] = count;
+  if (start < dplus) emit(start, dplus);
+  if (!WRITE && lane == 0) cnt[slot] = count;
 }
 
 __global__ void __launch_bounds__(1024) k_scan_counts(int32_t* data, int count) {
@@ -921,7 +941,7 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
   if (e != cudaSuccess) return e;
   const int ex = (int)std::min<int64_t>((p.entry_stride + 255) / 256, 4096);
   k_plan_est<K><<<dim3(ex, p.G), 256, 0, s>>>(graphs, p.entry_stride, est, x1s, hdr, rb, re);
-  const int rx = (p.nmax + 255) / 256;
+  const int rx = (p.nmax + 7) / 8;  // one warp per root, 8 per block
   const double target = (double)p.blocks * p.warps_per_block * kTargetItemsPerWarp;
   k_plan_items<K, false><<<dim3(rx, p.G), 256, 0, s>>>(graphs, p.entry_stride, est, x1s, p.nmax,
                                                        cnt, items, p.items_max, hdr, p.split_cost,
