@@ -52,6 +52,9 @@ struct Hdr {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kTargetItemsPerWarp = 64;
+// Adds one warp may make to a shared 32-bit histogram between two flushes of
+// it by exchange (enumeration path, k <= 5; see `ladd` in k_count).
+constexpr int kLeafBudget = 1 << 25;
 constexpr int kMaxWarpsPerBlock = 32;
 // Per-warp stack of suspended DFS levels: (cursor, choice end, tail end, key, vertex).
 constexpr int kLevelBytes = 128;
@@ -331,6 +334,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   __shared__ int s_cur_g;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = blockDim.x >> 5;
+  const unsigned lanes_below = (1u << lane) - 1u;
+  int since = 0;  // this warp's enumeration adds since its last flush
   unsigned char* sp = smem;
   int32_t* s_urow = (int32_t*)sp;
   uint32_t* s_ucol = (uint32_t*)(sp + (GC ? ((a.nmax + 1) * 4 + 15) / 16 * 16 : 0));
@@ -411,6 +416,33 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         }
       } else {
         atomicAdd(&ghist[id], (unsigned long long)delta);
+      }
+    };
+
+    // Positive adds of the enumeration path.  For k <= 5 the shared 32-bit
+    // counters take them without returning the old value; each warp counts
+    // what it added since it last flushed and, past kLeafBudget, moves the
+    // whole shared histogram to the graph's 64-bit counters by exchange
+    // (adds of other warps stay in the counters).  A counter then never holds
+    // more than warps x (kLeafBudget + one choice's adds) < 2^31.
+    auto ladd = [&](uint32_t id, int d) {
+      if (id >= C) {
+        atomicOr(w.err, kErrStackOverflow);
+        return;
+      }
+      if (K <= 5) atomicAdd(&s_hist[id], d);
+      else atomicAdd(&ghist[id], (unsigned long long)d);
+    };
+    auto leaf_budget = [&](int adds) {
+      if (K <= 5) {
+        if (since >= kLeafBudget) {
+          for (int i = lane; i < (int)C; i += 32) {
+            const int x = atomicExch(&s_hist[i], 0);
+            if (x) atomicAdd(&ghist[i], (unsigned long long)(long long)x);
+          }
+          since = 0;
+        }
+        since += adds;
       }
     };
 
@@ -612,18 +644,19 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             const int y = buf[c];
             cur_c = c + 1;
             const uint32_t P2 = key | ((uint32_t)lab[y] << (L * (L - 1)));
+            const int ys = w.urow[y], ye = w.urow[y + 1];
+            const int ystart = (ye - ys > 32) ? first_above_p(w.ucol, ys, ye, w.root) : ys;
+            leaf_budget((ye - ystart) + (e - c - 1));
             // (a) y's row: mark its relation bits; an exclusive neighbour u (no
             //     relation to the first k-2 vertices) completes a k-set whose key
             //     is fixed by the arc code between y and u
             {
-              const int rs = w.urow[y], re = w.urow[y + 1];
-              const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
               int n1 = 0, n2 = 0, n3 = 0;
-              for (int b = start; b < re; b += 32) {
+              for (int b = ystart; b < ye; b += 32) {
                 const int j = b + lane;
                 bool ex = false;
                 uint32_t code = 0;
-                if (j < re) {
+                if (j < ye) {
                   const uint32_t ent = w.ucol[j];
                   const int u = (int)(ent & kVertexMask);
                   code = ent >> 30;
@@ -640,7 +673,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
               __syncwarp();
               if (lane < 3) {
                 const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
-                if (cnt) hadd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+                if (cnt) ladd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
               }
             }
             // (b) the tail buf[c+1, e): relation words now include y's bits
@@ -651,20 +684,38 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
               const uint32_t l1 = v1 ? (uint32_t)lab[buf[i1]] : 0xFFFFFFFFu;
               const unsigned p0 = __match_any_sync(kFull, l0);
               const unsigned p1 = __match_any_sync(kFull, l1);
-              const bool lead0 = v0 && lane == __ffs(p0) - 1;
-              const bool lead1 = v1 && lane == __ffs(p1) - 1;
+              const bool lead0 = v0 && !(p0 & lanes_below);
+              const bool lead1 = v1 && !(p1 & lanes_below);
               uint32_t id0 = kNoClass, id1 = kNoClass;
               if (lead0) id0 = __ldg(&a.table[P2 | (l0 << OFF1)]);
               if (lead1) id1 = __ldg(&a.table[P2 | (l1 << OFF1)]);
-              if (lead0) hadd(id0, __popc(p0));
-              if (lead1) hadd(id1, __popc(p1));
+              if (lead0) ladd(id0, __popc(p0));
+              if (lead1) ladd(id1, __popc(p1));
             }
             // (c) unmark y
-            pop_vertex(w, y, L);
+            {
+              const LT clear = (LT)~(3u << NB);
+              for (int b = ystart; b < ye; b += 32) {
+                const int j = b + lane;
+                if (j < ye) {
+                  const int u = (int)(w.ucol[j] & kVertexMask);
+                  if (u > w.root) lab[u] &= clear;
+                }
+              }
+              __syncwarp();
+            }
             continue;
           }
           const int ng = min(GS, ce - c);
           cur_c = c + ng;
+          {
+            int adds = ng * (e - c - 1);
+            for (int gg = 0; gg < ng; ++gg) {
+              const int y = buf[c + gg];
+              adds += w.urow[y + 1] - w.urow[y];
+            }
+            leaf_budget(adds);
+          }
           uint32_t Pg = 0;  // key prefix of choice `lane`
           if (lane < ng) Pg = key | ((uint32_t)(lab[buf[c + lane]] & LM) << OFF2);
           // (a) each choice's row: mark its slot; an exclusive neighbour u (no
@@ -698,7 +749,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             const uint32_t pg = __shfl_sync(kFull, Pg, gg);
             if (lane < 3) {
               const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
-              if (cnt) hadd(__ldg(&a.table[pg | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
+              if (cnt) ladd(__ldg(&a.table[pg | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
             }
           }
           // (b) the candidates after the group's first choice; those after
@@ -713,8 +764,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
               const uint32_t wd = (lt & LM) | (((lt >> (NB + 2 * gg)) & 3u) << NB);
               const uint32_t pg = __shfl_sync(kFull, Pg, gg);
               const unsigned peers = __match_any_sync(kFull, vg ? wd : 0xFFFFFFFFu);
-              if (vg && lane == __ffs(peers) - 1)
-                hadd(__ldg(&a.table[pg | (wd << OFF1)]), __popc(peers));
+              if (vg && !(peers & lanes_below))
+                ladd(__ldg(&a.table[pg | (wd << OFF1)]), __popc(peers));
             }
           }
           // (c) clear the slots
@@ -757,6 +808,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     }
     // this graph's queue is empty: flush, then move to a graph with items left
     __syncthreads();
+    since = 0;
     if (K <= 5) {
       for (int i = tid; i < (int)C; i += blockDim.x) {
         const int32_t x = s_hist[i];
