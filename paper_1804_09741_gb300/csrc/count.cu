@@ -347,7 +347,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                           kLevelBytes);
   int* lvs = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
   using LT = LabT<K, COMB>;
-  LT* lab = LS ? (LT*)mine : (LT*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.nmax;
+  // each warp's relation words start on a 16-byte boundary (lab_bytes is a
+  // multiple of 16), so 32-bit atomics on them are aligned
+  LT* lab = LS ? (LT*)mine
+               : (LT*)((char*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.lab_bytes);
   uint16_t* buf = (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
   // combinatorial mode: per-cell counts (choices in the low, tail in the high
   // 16 bits), the list of non-empty cells, and its length
@@ -954,7 +957,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->off_cnt = off; off += round16(((size_t)G * nmax + 1) * 4);
   p->off_items = off; off += round16(p->items_max * sizeof(Item));
   p->off_lab = off;
-  if (!p->lab_smem) off += round16((size_t)p->blocks * p->warps_per_block * nmax * lab_elem);
+  if (!p->lab_smem) off += (size_t)p->blocks * p->warps_per_block * lab_bytes;
   p->ws_bytes = off + 256;
   return MT_OK;
 }
@@ -1005,8 +1008,7 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
                                                       p.split_scale, target, p.items_factor, rb,
                                                       re);
   if (!p.lab_smem) {
-    e = cudaMemsetAsync(lab, 0,
-                        (size_t)p.blocks * p.warps_per_block * p.nmax * (K <= 5 ? 1 : 2), s);
+    e = cudaMemsetAsync(lab, 0, (size_t)p.blocks * p.warps_per_block * p.lab_bytes, s);
     if (e != cudaSuccess) return e;
   }
   CountArgs a;

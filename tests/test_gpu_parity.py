@@ -128,6 +128,33 @@ def test_medium_power_law_graphs(lib, tables, k, method):
     check_against_oracle(lib, tables(k), g, k, method=method)
 
 
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_large_graph_relation_words_in_global_memory(lib, tables, k, method):
+    """n = 20,000: one warp's relation words (n bytes, 2n at k = 6) cannot sit
+    in shared memory beside 16 warps' stacks, so the launch keeps them in
+    global memory, one 16-byte-aligned slice per warp (the k = 5 enumerator
+    updates them with 32-bit atomics).  k = 4, 5 against the whole oracle
+    histogram; k = 6 on root ranges away from the hubs, plus the property that
+    disjoint ranges add up to the whole count (of either method)."""
+    g = syn.chung_lu_digraph(20000, 24000, 2.5, 30, 0.1, 77)
+    t = tables(k)
+    if k <= 5:
+        check_against_oracle(lib, t, g, k, method=method)
+        return
+    dg = lib.graph_from(g)
+    cm = t.class_masks()
+    for a, b in [(800, 850), (1500, 1600), (3000, 3200)]:
+        want, sets = oracle.count_roots(g, 6, np.arange(a, b))
+        h = lib.count_roots(dg, t, a, b)
+        assert int(h.sum()) == sets
+        np.testing.assert_array_equal(h, oracle_dense(want, cm))
+    full = lib.to_numpy_u64(lib.count_tuned(dg, t, method=method))
+    assert lib.count_stats(dg)[1] == 0
+    parts = sum(lib.count_roots(dg, t, a, b) for a, b in [(0, 800), (800, 850), (850, 20000)])
+    np.testing.assert_array_equal(parts, full)
+
+
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
 @pytest.mark.parametrize("split", [1.0, 1e12])
 @pytest.mark.parametrize("wpb", [1, 16])
