@@ -282,7 +282,7 @@ static mt_status batch_run(mt_batch* b, const uint64_t* seeds, uint64_t* hists, 
     MT_CUDA_TRY(cudaStreamSynchronize(s));
     uint32_t err = 0;
     MT_CUDA_TRY(cudaMemcpy(&err, count_err_ptr(b->plan, b->ws), 4, cudaMemcpyDeviceToHost));
-    if (err) return MT_EOVERFLOW;
+    if (err) return (err & kErrWaitLimit) ? MT_ETIMEOUT : MT_EOVERFLOW;
   }
   return MT_OK;
 }

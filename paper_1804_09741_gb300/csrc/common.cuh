@@ -19,6 +19,7 @@ constexpr uint32_t kNumClasses[7] = {0, 1, 2, 13, 199, 9364, 1530843};
 // Error bits written by kernels into a device status word.
 constexpr uint32_t kErrStackOverflow = 1u;
 constexpr uint32_t kErrDuplicateArc = 2u;
+constexpr uint32_t kErrWaitLimit = 4u;  // a bounded device wait gave up
 
 // Undirected neighbour entry: vertex id in bits 0..29, bit 30 set iff the arc
 // row-vertex -> neighbour exists, bit 31 set iff neighbour -> row-vertex exists

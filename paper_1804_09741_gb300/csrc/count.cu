@@ -55,6 +55,19 @@ constexpr int kTargetItemsPerWarp = 64;
 // Adds one warp may make to a shared 32-bit histogram between two flushes of
 // it by exchange (enumeration path, k <= 5; see `ladd` in k_count).
 constexpr int kLeafBudget = 1 << 25;
+// Items a block's warps can hand to each other at once (work donation).
+constexpr int kDonSlots = 32;
+// Bounds of the waits of work donation: lock attempts, idle polls, and the
+// idle time (ns) after which a warp gives up and reports kErrWaitLimit.
+constexpr int kLockTries = 1 << 24;
+constexpr int kIdlePolls = 1 << 28;
+constexpr unsigned long long kIdleNs = 60ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 constexpr int kMaxWarpsPerBlock = 32;
 // Per-warp stack of suspended DFS levels: (cursor, choice end, tail end, key, vertex).
 constexpr int kLevelBytes = 128;
@@ -325,13 +338,18 @@ template <int K>
 constexpr int kCells = 1 << (2 * (K - 2));
 
 // Persistent enumerator.  A thread block works on one graph at a time: its
-// warps take that graph's items from the graph's queue; when the queue is
-// empty the block flushes its shared histogram, picks the next graph that still
-// has items and (GC) copies that graph's CSR into shared memory.
+// warps take that graph's items from the graph's queue.  A warp that finds the
+// queue empty waits for work donated by the block's other warps: a busy warp
+// that sees an idle one hands over half of its remaining first- or
+// second-level choices as a new item.  When every warp is idle and nothing is
+// left to take, the block flushes its shared histogram, picks the next graph
+// that still has items and (GC) copies that graph's CSR into shared memory.
 template <int K, bool GC, bool LS, bool COMB>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_cur_g;
+  __shared__ int s_idle, s_ndon, s_lock;  // work donation (see above)
+  __shared__ uint32_t s_don[kDonSlots * 4];  // donated items, 4 words each
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = blockDim.x >> 5;
   const unsigned lanes_below = (1u << lane) - 1u;
@@ -369,8 +387,33 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   }
   if (K <= 5)
     for (int i = tid; i < (int)C; i += blockDim.x) s_hist[i] = 0;
-  if (tid == 0) s_cur_g = (int)(((int64_t)blockIdx.x * a.G) / gridDim.x);
+  if (tid == 0) {
+    s_cur_g = (int)(((int64_t)blockIdx.x * a.G) / gridDim.x);
+    s_idle = 0;
+    s_ndon = 0;
+    s_lock = 0;
+  }
   __syncthreads();
+
+  // Block-local lock of the donation slots (lane 0 of a warp only).
+  auto block_lock = [&]() -> bool {
+    for (int i = 0; i < kLockTries; ++i) {
+      if (atomicCAS(&s_lock, 0, 1) == 0) {
+        __threadfence_block();
+        return true;
+      }
+      __nanosleep(32);
+    }
+    atomicOr(&a.hdr->err, kErrWaitLimit);
+    return false;
+  };
+  auto block_unlock = [&]() {
+    __threadfence_block();
+    atomicExch(&s_lock, 0);
+  };
+  volatile int* v_idle = &s_idle;
+  volatile int* v_ndon = &s_ndon;
+  volatile uint32_t* v_don = s_don;
 
   WarpCtx<LT> w;
   w.lab = lab;
@@ -571,13 +614,64 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       __syncwarp();
     };
 
-    while (true) {
+    // Lane 0: wait, idle, for a donated item (1) or for the whole block to be
+    // idle with nothing left to take (0).
+    auto take_donation = [&](uint4& raw) -> int {
+      if (!block_lock()) return 0;
+      *v_idle = *v_idle + 1;
+      block_unlock();
+      const unsigned long long t0 = global_ns();
+      for (int poll = 0; poll < kIdlePolls; ++poll) {
+        if (*v_ndon > 0 || *v_idle == nwarps) {
+          if (!block_lock()) return 0;
+          int r = -1;
+          const int nd = *v_ndon;
+          if (nd > 0) {
+            raw.x = v_don[4 * (nd - 1)];
+            raw.y = v_don[4 * (nd - 1) + 1];
+            raw.z = v_don[4 * (nd - 1) + 2];
+            raw.w = v_don[4 * (nd - 1) + 3];
+            *v_ndon = nd - 1;
+            *v_idle = *v_idle - 1;
+            r = 1;
+          } else if (*v_idle == nwarps) {
+            r = 0;
+          }
+          block_unlock();
+          if (r >= 0) return r;
+        }
+        if (global_ns() - t0 > kIdleNs) break;
+        __nanosleep(256);
+      }
+      atomicOr(&a.hdr->err, kErrWaitLimit);
+      return 0;
+    };
+    // The warp's next item: the graph's queue, then donated items.
+    auto next_item = [&](Item& out) -> bool {
       uint32_t idx = 0;
       if (lane == 0) idx = atomicAdd(&a.qhead[g], 1u);
       idx = __shfl_sync(kFull, idx, 0);
       const int64_t pos = (int64_t)ib + idx;
-      if (pos >= ie) break;
-      const Item it = a.items[pos];
+      if (pos < ie) {
+        out = a.items[pos];
+        return true;
+      }
+      uint4 raw = make_uint4(0, 0, 0, 0);
+      int got = 0;
+      if (lane == 0) got = take_donation(raw);
+      got = __shfl_sync(kFull, got, 0);
+      if (!got) return false;
+      raw.x = __shfl_sync(kFull, raw.x, 0);
+      raw.y = __shfl_sync(kFull, raw.y, 0);
+      raw.z = __shfl_sync(kFull, raw.z, 0);
+      raw.w = __shfl_sync(kFull, raw.w, 0);
+      memcpy(&out, &raw, sizeof(Item));
+      return true;
+    };
+
+    while (true) {
+      Item it;
+      if (!next_item(it)) break;
       const int v = (int)it.root;
       w.root = v;
       const int re = w.urow[v + 1];
@@ -776,13 +870,60 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           continue;
         }
         if (c < ce) {
+          // work donation: with an idle warp in the block, hand the second
+          // half of this level's remaining choices over as a new item (a
+          // first-level range, or a second-level range under the current
+          // first-level choice)
+          int cee = ce;
+          if (L <= 2 && L < K - 2 && ce - c >= 2) {
+            int hungry = 0;
+            if (lane == 0) hungry = *v_idle > 0 && *v_ndon < kDonSlots;
+            hungry = __shfl_sync(kFull, hungry, 0);
+            if (hungry) {
+              const int mid = c + (ce - c + 1) / 2;
+              int ok = 0;
+              if (lane == 0) {
+                Item d;
+                d.g = (uint32_t)g;
+                d.root = (uint32_t)v;
+                if (L == 1) {
+                  d.j1a = (uint16_t)(j1a + mid);
+                  d.j1b = (uint16_t)(j1a + ce);
+                  d.a2 = 0;
+                  d.b2 = 0xFFFF;
+                } else {
+                  const int c1 = lvs[5] - 1;  // index of the first-level choice
+                  d.j1a = (uint16_t)(j1a + c1);
+                  d.j1b = (uint16_t)(j1a + c1 + 1);
+                  d.a2 = (uint16_t)(mid - (c1 + 1));
+                  d.b2 = (uint16_t)(ce - (c1 + 1));
+                }
+                if (block_lock()) {
+                  const int nd = *v_ndon;
+                  if (nd < kDonSlots) {
+                    uint4 raw;
+                    memcpy(&raw, &d, sizeof(Item));
+                    v_don[4 * nd] = raw.x;
+                    v_don[4 * nd + 1] = raw.y;
+                    v_don[4 * nd + 2] = raw.z;
+                    v_don[4 * nd + 3] = raw.w;
+                    *v_ndon = nd + 1;
+                    ok = 1;
+                  }
+                  block_unlock();
+                }
+              }
+              ok = __shfl_sync(kFull, ok, 0);
+              if (ok) cee = mid;
+            }
+          }
           const int x = buf[c];
           const uint32_t nkey = key | ((uint32_t)lab[x] << (L * (L - 1)));
           const int ne = push_vertex(w, x, L, e);
           if (lane == 0) {
             int* sv = lvs + 5 * L;
             sv[0] = c + 1;
-            sv[1] = ce;
+            sv[1] = cee;
             sv[2] = e;
             sv[3] = (int)key;
             sv[4] = x;
@@ -822,6 +963,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       }
     }
     if (tid == 0) {
+      s_idle = 0;
+      s_ndon = 0;
       int next = -1;
       for (int t = 1; t <= a.G; ++t) {
         const int g2 = (g + t) % a.G;
@@ -1108,7 +1251,7 @@ static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist
     uint32_t err = 0;
     MT_CUDA_TRY(cudaMemcpyAsync(&err, base + g->off_err, 4, cudaMemcpyDeviceToHost, s));
     MT_CUDA_TRY(cudaStreamSynchronize(s));
-    if (err) return MT_EOVERFLOW;
+    if (err) return (err & kErrWaitLimit) ? MT_ETIMEOUT : MT_EOVERFLOW;
   }
   return MT_OK;
 }
