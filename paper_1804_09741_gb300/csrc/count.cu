@@ -269,10 +269,12 @@ __device__ __forceinline__ int first_above_p(const uint32_t* ucol, int lo, int h
 }
 
 // Push x at position p: OR its relation bits into lab[] of its neighbours above
-// the root and append the exclusive ones (relation word was zero) at stack
-// index e.  Returns the new end of the candidate list.
+// the root and append the exclusive ones (no relation to positions 0..p-1, the
+// bits in `low`; bits above it may be stale) at stack index e.  Returns the
+// new end of the candidate list.
 template <typename LT>
-__device__ __forceinline__ int push_vertex(const WarpCtx<LT>& w, int x, int p, int e) {
+__device__ __forceinline__ int push_vertex(const WarpCtx<LT>& w, int x, int p, int e,
+                                           uint32_t low) {
   const int rs = w.urow[x], re = w.urow[x + 1];
   const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
   const unsigned lt = (1u << w.lane) - 1u;
@@ -287,7 +289,7 @@ __device__ __forceinline__ int push_vertex(const WarpCtx<LT>& w, int x, int p, i
       if (u > w.root) {
         const LT old = w.lab[u];
         w.lab[u] = (LT)(old | ((ent >> 30) << (2 * p)));
-        ex = (old == 0);
+        ex = ((uint32_t)old & low) == 0;
       }
     }
     const unsigned bal = __ballot_sync(kFull, ex);
@@ -700,6 +702,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       int cur_c = 0, cur_ce = min(j1b - j1a, cur_e);
       uint32_t cur_key = 0;
       const bool has2 = it.b2 != 0xFFFF;
+      // The enumerator's slot codes (bits of positions k-2 and up) are not
+      // cleared by row scans: the tail pass writes each candidate back
+      // without them, and a candidate list is cleaned once when its level
+      // (k-2 positions chosen) is entered; every other reader masks them.
+      bool fresh = true;
       int L = 1;
       auto pop_level = [&]() {
         L -= 1;
@@ -734,13 +741,25 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           constexpr uint32_t LM = (1u << NB) - 1u;
           constexpr int OFF1 = (K - 1) * (K - 2);
           constexpr int OFF2 = (K - 2) * (K - 3);
+          if (fresh) {
+            // a new candidate list: clear slot codes left by earlier rows
+            for (int b = c; b < e; b += 32) {
+              const int i = b + lane;
+              if (i < e) {
+                const int u = buf[i];
+                lab[u] = (LT)((uint32_t)lab[u] & LM);
+              }
+            }
+            __syncwarp();
+            fresh = false;
+          }
           // slots left in the relation word above the first k-2 positions
           constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 4 ? (8 * (int)sizeof(LT) - NB) / 2 : 4;
           if constexpr (GS == 1) {
             // one choice at a time, two batches of leaves in flight
             const int y = buf[c];
             cur_c = c + 1;
-            const uint32_t P2 = key | ((uint32_t)lab[y] << (L * (L - 1)));
+            const uint32_t P2 = key | (((uint32_t)lab[y] & LM) << (L * (L - 1)));
             const int ys = w.urow[y], ye = w.urow[y + 1];
             const int ystart = (ye - ys > 32) ? first_above_p(w.ucol, ys, ye, w.root) : ys;
             leaf_budget((ye - ystart) + (e - c - 1));
@@ -760,7 +779,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                   if (u > w.root) {
                     const LT old = lab[u];
                     lab[u] = (LT)(old | (code << NB));
-                    ex = old == 0;
+                    ex = ((uint32_t)old & LM) == 0;
                   }
                 }
                 n1 += __popc(__ballot_sync(kFull, ex && code == 1));
@@ -773,12 +792,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                 if (cnt) ladd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
               }
             }
-            // (b) the tail buf[c+1, e): relation words now include y's bits
+            // (b) the tail buf[c+1, e): relation words now include y's bits,
+            //     which are cleared again as they are read
             for (int b = c + 1; b < e; b += 64) {
               const int i0 = b + lane, i1 = b + 32 + lane;
               const bool v0 = i0 < e, v1 = i1 < e;
-              const uint32_t l0 = v0 ? (uint32_t)lab[buf[i0]] : 0xFFFFFFFFu;
-              const uint32_t l1 = v1 ? (uint32_t)lab[buf[i1]] : 0xFFFFFFFFu;
+              const int u0 = v0 ? buf[i0] : 0, u1 = v1 ? buf[i1] : 0;
+              const uint32_t l0 = v0 ? (uint32_t)lab[u0] : 0xFFFFFFFFu;
+              const uint32_t l1 = v1 ? (uint32_t)lab[u1] : 0xFFFFFFFFu;
+              if (v0) lab[u0] = (LT)(l0 & LM);
+              if (v1) lab[u1] = (LT)(l1 & LM);
               const unsigned p0 = __match_any_sync(kFull, l0);
               const unsigned p1 = __match_any_sync(kFull, l1);
               const bool lead0 = v0 && !(p0 & lanes_below);
@@ -789,18 +812,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
               if (lead0) ladd(id0, __popc(p0));
               if (lead1) ladd(id1, __popc(p1));
             }
-            // (c) unmark y
-            {
-              const LT clear = (LT)~(3u << NB);
-              for (int b = ystart; b < ye; b += 32) {
-                const int j = b + lane;
-                if (j < ye) {
-                  const int u = (int)(w.ucol[j] & kVertexMask);
-                  if (u > w.root) lab[u] &= clear;
-                }
-              }
-              __syncwarp();
-            }
+            __syncwarp();
             continue;
           }
           const int ng = min(GS, ce - c);
@@ -855,7 +867,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           for (int b = c + 1; b < e; b += 32) {
             const int i0 = b + lane;
             const bool v0 = i0 < e;
-            const uint32_t lt = v0 ? (uint32_t)lab[buf[i0]] : 0u;
+            const int u0 = v0 ? buf[i0] : 0;
+            const uint32_t lt = v0 ? (uint32_t)lab[u0] : 0u;
+            if (v0) lab[u0] = (LT)(lt & LM);
             for (int gg = 0; gg < ng; ++gg) {
               const bool vg = v0 && i0 > c + gg;
               const uint32_t wd = (lt & LM) | (((lt >> (NB + 2 * gg)) & 3u) << NB);
@@ -865,8 +879,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                 ladd(__ldg(&a.table[pg | (wd << OFF1)]), __popc(peers));
             }
           }
-          // (c) clear the slots
-          for (int gg = 0; gg < ng; ++gg) pop_vertex(w, buf[c + gg], L + gg);
+          __syncwarp();
           continue;
         }
         if (c < ce) {
@@ -918,8 +931,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             }
           }
           const int x = buf[c];
-          const uint32_t nkey = key | ((uint32_t)lab[x] << (L * (L - 1)));
-          const int ne = push_vertex(w, x, L, e);
+          const uint32_t nkey = key | (((uint32_t)lab[x] & ((1u << (2 * L)) - 1u)) << (L * (L - 1)));
+          const int ne = push_vertex(w, x, L, e, (1u << (2 * (K - 2))) - 1u);
           if (lane == 0) {
             int* sv = lvs + 5 * L;
             sv[0] = c + 1;
@@ -938,6 +951,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             cur_ce = min(c + 1 + (int)it.b2, ne);
           }
           L += 1;
+          if (L == K - 2) fresh = true;
         } else {
           if (L == 1) break;
           pop_level();
