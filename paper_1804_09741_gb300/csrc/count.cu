@@ -817,49 +817,55 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           }
           const int ng = min(GS, ce - c);
           cur_c = c + ng;
-          {
-            int adds = ng * (e - c - 1);
-            for (int gg = 0; gg < ng; ++gg) {
-              const int y = buf[c + gg];
-              adds += w.urow[y + 1] - w.urow[y];
-            }
-            leaf_budget(adds);
+          // lane g < ng: choice g's key prefix and its row above the root
+          uint32_t Pg = 0;
+          int rs_g = 0, len_g = 0;
+          if (lane < ng) {
+            const int y = buf[c + lane];
+            Pg = key | ((uint32_t)(lab[y] & LM) << OFF2);
+            const int r0 = w.urow[y], r1 = w.urow[y + 1];
+            rs_g = (r1 - r0 > 32) ? first_above_p(w.ucol, r0, r1, w.root) : r0;
+            len_g = r1 - rs_g;
           }
-          uint32_t Pg = 0;  // key prefix of choice `lane`
-          if (lane < ng) Pg = key | ((uint32_t)(lab[buf[c + lane]] & LM) << OFF2);
-          // (a) each choice's row: mark its slot; an exclusive neighbour u (no
-          //     relation to the first k-2 vertices) completes a k-set whose
-          //     key is fixed by the arc code between the choice and u
-          for (int gg = 0; gg < ng; ++gg) {
-            const int y = buf[c + gg];
-            const int rs = w.urow[y], re = w.urow[y + 1];
-            const int start = (re - rs > 32) ? first_above_p(w.ucol, rs, re, w.root) : rs;
-            const int sh = NB + 2 * gg;
-            int n1 = 0, n2 = 0, n3 = 0;
-            for (int b = start; b < re; b += 32) {
-              const int j = b + lane;
+          const int q1 = __shfl_sync(kFull, len_g, 0);
+          const int q2 = q1 + __shfl_sync(kFull, len_g, 1);
+          const int q3 = q2 + __shfl_sync(kFull, len_g, 2);
+          const int tot = q3 + __shfl_sync(kFull, len_g, 3);
+          leaf_budget(ng * (e - c - 1) + tot);
+          // (a) the group's rows, concatenated over the lanes: choice g sets
+          //     slot g of its neighbours (a 32-bit atomic OR on the word that
+          //     holds the relation word, as two choices may share a
+          //     neighbour); an exclusive neighbour u (no relation to the first
+          //     k-2 vertices) completes a k-set keyed by the choice's prefix
+          //     and the arc code between the choice and u, counted per
+          //     (choice, code) group of the pass
+          {
+            constexpr int PER = 4 / (int)sizeof(LT);  // relation words per 32-bit word
+            uint32_t* lab32 = (uint32_t*)lab;
+            for (int b = 0; b < tot; b += 32) {
+              const int q = b + lane;
+              const int gg = (q >= q1) + (q >= q2) + (q >= q3);
+              const int rs = __shfl_sync(kFull, rs_g, gg & 3);
+              const uint32_t pg = __shfl_sync(kFull, Pg, gg & 3);
               bool ex = false;
               uint32_t code = 0;
-              if (j < re) {
-                const uint32_t ent = w.ucol[j];
+              if (q < tot) {
+                const int off = gg == 0 ? 0 : (gg == 1 ? q1 : (gg == 2 ? q2 : q3));
+                const uint32_t ent = w.ucol[rs + (q - off)];
                 const int u = (int)(ent & kVertexMask);
                 code = ent >> 30;
                 if (u > w.root) {
-                  const LT old = lab[u];
-                  lab[u] = (LT)(old | (code << sh));
+                  const uint32_t old = (uint32_t)lab[u];
+                  atomicOr(&lab32[u / PER],
+                           (code << (NB + 2 * gg)) << (8 * (int)sizeof(LT) * (u % PER)));
                   ex = (old & LM) == 0;
                 }
               }
-              n1 += __popc(__ballot_sync(kFull, ex && code == 1));
-              n2 += __popc(__ballot_sync(kFull, ex && code == 2));
-              n3 += __popc(__ballot_sync(kFull, ex && code == 3));
+              const unsigned peers = __match_any_sync(kFull, ex ? (uint32_t)(gg * 4) + code : 0xFFFFFFFFu);
+              if (ex && !(peers & lanes_below))
+                ladd(__ldg(&a.table[pg | ((code << NB) << OFF1)]), __popc(peers));
             }
             __syncwarp();
-            const uint32_t pg = __shfl_sync(kFull, Pg, gg);
-            if (lane < 3) {
-              const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
-              if (cnt) ladd(__ldg(&a.table[pg | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
-            }
           }
           // (b) the candidates after the group's first choice; those after
           //     choice g are its leaves, keyed by their word to the first k-2
