@@ -243,9 +243,12 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int32_t* data, int count) 
 
 // ------------------------------------------------------------------ enumerator
 
-// Relation words: 2 bits per earlier position, k-1 positions -> 8 bits for k <= 5.
+// Relation words: 2 bits per earlier position.  The first k-2 positions take
+// 2(k-2) bits; the slots above them let several (k-1)-th choices be marked at
+// once: 8 bits for k <= 4 (3 and 2 slots), 16 bits for k = 5, 6 (4 slots each).
+// The cell method needs only two flag bits above them: 8 bits up to k = 5.
 template <int K, bool CB>
-using LabT = typename std::conditional<(K <= 5), uint8_t, uint16_t>::type;
+using LabT = typename std::conditional<(K <= 4 || (CB && K <= 5)), uint8_t, uint16_t>::type;
 
 template <typename LT>
 struct WarpCtx {
@@ -729,9 +732,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         if (!COMB && L == K - 2) {
           // Choosing the (k-1)-th vertex finishes its k-sets in place, for up
           // to GS consecutive choices at once (as many as the relation word
-          // has free 2-bit slots: 3, 2, 1, 4 for k = 3..6): choice g marks its
-          // row into slot g above the first k-2 positions' bits, so one pass
-          // over the shared candidate tail classifies every choice's leaves.
+          // has free 2-bit slots, at most 4: 3, 2, 4, 4 for k = 3..6): choice
+          // g marks its row into slot g above the first k-2 positions' bits,
+          // so one pass over the shared candidate tail classifies every
+          // choice's leaves.
           if (c >= ce) {
             if (L == 1) break;
             pop_level();
@@ -755,66 +759,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           }
           // slots left in the relation word above the first k-2 positions
           constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 4 ? (8 * (int)sizeof(LT) - NB) / 2 : 4;
-          if constexpr (GS == 1) {
-            // one choice at a time, two batches of leaves in flight
-            const int y = buf[c];
-            cur_c = c + 1;
-            const uint32_t P2 = key | (((uint32_t)lab[y] & LM) << (L * (L - 1)));
-            const int ys = w.urow[y], ye = w.urow[y + 1];
-            const int ystart = (ye - ys > 32) ? first_above_p(w.ucol, ys, ye, w.root) : ys;
-            leaf_budget((ye - ystart) + (e - c - 1));
-            // (a) y's row: mark its relation bits; an exclusive neighbour u (no
-            //     relation to the first k-2 vertices) completes a k-set whose key
-            //     is fixed by the arc code between y and u
-            {
-              int n1 = 0, n2 = 0, n3 = 0;
-              for (int b = ystart; b < ye; b += 32) {
-                const int j = b + lane;
-                bool ex = false;
-                uint32_t code = 0;
-                if (j < ye) {
-                  const uint32_t ent = w.ucol[j];
-                  const int u = (int)(ent & kVertexMask);
-                  code = ent >> 30;
-                  if (u > w.root) {
-                    const LT old = lab[u];
-                    lab[u] = (LT)(old | (code << NB));
-                    ex = ((uint32_t)old & LM) == 0;
-                  }
-                }
-                n1 += __popc(__ballot_sync(kFull, ex && code == 1));
-                n2 += __popc(__ballot_sync(kFull, ex && code == 2));
-                n3 += __popc(__ballot_sync(kFull, ex && code == 3));
-              }
-              __syncwarp();
-              if (lane < 3) {
-                const int cnt = lane == 0 ? n1 : (lane == 1 ? n2 : n3);
-                if (cnt) ladd(__ldg(&a.table[P2 | (((uint32_t)(lane + 1) << NB) << OFF1)]), cnt);
-              }
-            }
-            // (b) the tail buf[c+1, e): relation words now include y's bits,
-            //     which are cleared again as they are read
-            for (int b = c + 1; b < e; b += 64) {
-              const int i0 = b + lane, i1 = b + 32 + lane;
-              const bool v0 = i0 < e, v1 = i1 < e;
-              const int u0 = v0 ? buf[i0] : 0, u1 = v1 ? buf[i1] : 0;
-              const uint32_t l0 = v0 ? (uint32_t)lab[u0] : 0xFFFFFFFFu;
-              const uint32_t l1 = v1 ? (uint32_t)lab[u1] : 0xFFFFFFFFu;
-              if (v0) lab[u0] = (LT)(l0 & LM);
-              if (v1) lab[u1] = (LT)(l1 & LM);
-              const unsigned p0 = __match_any_sync(kFull, l0);
-              const unsigned p1 = __match_any_sync(kFull, l1);
-              const bool lead0 = v0 && !(p0 & lanes_below);
-              const bool lead1 = v1 && !(p1 & lanes_below);
-              uint32_t id0 = kNoClass, id1 = kNoClass;
-              if (lead0) id0 = __ldg(&a.table[P2 | (l0 << OFF1)]);
-              if (lead1) id1 = __ldg(&a.table[P2 | (l1 << OFF1)]);
-              if (lead0) ladd(id0, __popc(p0));
-              if (lead1) ladd(id1, __popc(p1));
-            }
-            __syncwarp();
-            continue;
-          }
+          static_assert(COMB || GS >= 2, "at least two slots per relation word");
           const int ng = min(GS, ce - c);
           cur_c = c + ng;
           // lane g < ng: choice g's key prefix and its row above the root
@@ -1059,7 +1004,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
   p->comb = tuning && tuning->method == MT_METHOD_CELLS;
-  const size_t lab_elem = K <= 5 ? 1 : 2;
+  const size_t lab_elem = (K <= 4 || (p->comb && K <= 5)) ? 1 : 2;
   const size_t lab_bytes = round16((size_t)nmax * lab_elem);
   const size_t cells = (size_t)1 << (2 * (K - 2));
   const size_t cell_bytes =
@@ -1074,25 +1019,28 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   const size_t budget = (size_t)max_smem - 1024;
   const int want = warps_per_block > 0 ? std::min(warps_per_block, kMaxWarpsPerBlock)
                                        : kMaxWarpsPerBlock;
-  // Preference: graph copy and relation words in shared memory with >= 16 warps,
-  // then relation words only, then graph only, then neither.
+  // Layout: the one that fits the most warps (>= 16 if any does), and on a tie
+  // the first of: graph copy and relation words in shared memory, relation
+  // words only, graph only, neither.  More warps beat the graph copy: rows
+  // read through L1 cost less than the warps the copy displaces.
   struct Opt { bool gc, ls; };
   const Opt opts[4] = {{true, true}, {false, true}, {true, false}, {false, false}};
   bool found = false;
   for (int pass = 0; pass < 2 && !found; ++pass) {
     const int min_w = pass == 0 ? std::min(want, 16) : 1;
+    int best_w = 0;
     for (const Opt& o : opts) {
       const size_t fixed = (o.gc ? graph_bytes : 0) + hist_bytes;
       const size_t per = (o.ls ? lab_bytes : 0) + buf_bytes;
       int w = want;
       while (w > min_w && fixed + (size_t)w * per > budget) --w;
-      if (fixed + (size_t)w * per <= budget) {
+      if (fixed + (size_t)w * per <= budget && w > best_w) {
         p->gcache = o.gc;
         p->lab_smem = o.ls;
         p->warps_per_block = w;
         p->smem_bytes = fixed + (size_t)w * per;
         found = true;
-        break;
+        best_w = w;
       }
     }
   }
