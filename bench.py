@@ -27,8 +27,10 @@ sys.path.insert(0, ROOT)
 
 import synthetic as syn  # noqa: E402
 
-# Root sample the CPU oracle times (k-sets whose smallest vertex is in it).
-CPU_SAMPLE = {"nullmodel_k5": (200, 232), "nullmodel_k6": (200, 220), "chunglu_k4": (0, 2000),
+# Root sample the CPU oracle times (k-sets whose smallest vertex is in it):
+# about 10-15 s of oracle work on 16 host cores for the two null-model
+# workloads (7.7e7 and 7.0e6 k-sets), the whole graph for the small ones.
+CPU_SAMPLE = {"nullmodel_k5": (60, 200), "nullmodel_k6": (100, 200), "chunglu_k4": (0, 2000),
               "uniform_k3": (0, 300)}
 INT32_LANES_PER_SM = 128
 
@@ -342,16 +344,8 @@ def run_ours(args, world, rank, local):
 
     gar = None
     if rank == 0 and R and count_ms:
-        # ceilings of one random table read and one random histogram add per
-        # subgraph (k=5 table: 2^20 words; a histogram of 9,364 -> 2^14 counters)
-        gps, aps = mt.probe_rates(1 << 20, 1 << 14)
         sub_rate = subgraphs_per_step / (statistics.mean(count_ms) / 1000.0)
-        gar = {"gather_peak_per_s": gps, "atomic_peak_per_s": aps,
-               "kernel_subgraphs_per_s": sub_rate, "frac_of_gather": sub_rate / gps,
-               "frac_of_atomic": sub_rate / aps,
-               "note": "per-subgraph ceilings: one random 4 B read from a 4 MB table and one "
-                       "random 64-bit atomic add per classified subgraph (mt_probe_rates, "
-                       "measured in this run); grouping equal keys lets the kernel exceed them"}
+        gar = _ceilings(mt, k, sub_rate)
 
     if rank == 0:
         line = {"metric": "k-subgraphs classified/s", "value": value, "unit": "subgraphs/s",
@@ -388,6 +382,28 @@ def _timed(torch, fn, steps, flush):
     return total
 
 
+def _ceilings(mt, k, sub_rate):
+    """The count kernel's rate against the measured ceilings of one random
+    table read (table of 2^(k(k-1)) words, as the k-vertex table) and one
+    random 64-bit histogram add (counters: the class count rounded up to a
+    power of two) per classified subgraph."""
+    table_words = 1 << (k * (k - 1))
+    hist_words = 1 << (int(syn_classes(k)) - 1).bit_length()
+    gps, aps = mt.probe_rates(table_words, hist_words)
+    return {"gather_peak_per_s": gps, "atomic_peak_per_s": aps,
+            "kernel_subgraphs_per_s": sub_rate, "frac_of_gather": sub_rate / gps,
+            "frac_of_atomic": sub_rate / aps, "table_bytes": 4 * table_words,
+            "hist_counters": hist_words,
+            "note": "per-subgraph ceilings: one random 4 B read from the k-vertex table and one "
+                    "random 64-bit atomic add per classified subgraph (mt_probe_rates, measured "
+                    "in this run); grouping equal keys and cache locality let the kernel exceed "
+                    "them"}
+
+
+def syn_classes(k):
+    return {3: 13, 4: 199, 5: 9364, 6: 1530843}[k]
+
+
 def measure_k6(mt, torch, steps=3, warmup=3):
     """The k=6 null-model batch: Chung-Lu n=800, m=3,200 plus 64 nulls."""
     w = syn.WORKLOADS["nullmodel_k6"]
@@ -406,10 +422,17 @@ def measure_k6(mt, torch, steps=3, warmup=3):
     torch.cuda.synchronize()
     sub = int(mt.to_numpy_u64(hists).sum())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ms = _timed(torch, lambda: b.run(seeds, hists, z), steps, flush)
+    ms = 0.0
+    count_ms = []
+    for _ in range(steps):
+        ms += _timed(torch, lambda: b.run(seeds, hists, z), 1, flush)
+        count_ms.append(b.phase_ms()[1])
+    cm = statistics.mean(count_ms)
     out = {"value": sub * steps / (ms / 1000.0), "unit": "subgraphs/s",
            "graphs_per_s": (R + 1) * steps / (ms / 1000.0), "ms_per_step": ms / steps,
-           "subgraphs_per_step": sub, "graphs_per_step": R + 1, "table_build_ms": table_ms,
+           "count_kernel_ms": cm, "subgraphs_per_step": sub, "graphs_per_step": R + 1,
+           "table_build_ms": table_ms,
+           "gather_atomic_roofline": _ceilings(mt, 6, sub / (cm / 1000.0)),
            "config": "Chung-Lu n=800 m=3200 gamma 2.5 dmax 40 r 0.10 + 64 nulls, k=6"}
     b.free()
     t.free()

@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     if (lane == 0) *ncell = 0;
   }
   if (K <= 5)
-    for (int i = tid; i < (int)C; i += blockDim.x) s_hist[i] = 0;
+    for (int i = tid; i <= (int)C; i += blockDim.x) s_hist[i] = 0;  // C: catch slot
   if (tid == 0) {
     s_cur_g = (int)(((int64_t)blockIdx.x * a.G) / gridDim.x);
     s_idle = 0;
@@ -476,13 +476,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     // whole shared histogram to the graph's 64-bit counters by exchange
     // (adds of other warps stay in the counters).  A counter then never holds
     // more than warps x (kLeafBudget + one choice's adds) < 2^31.
+    // (An id out of range, which a valid table never holds, lands in the
+    // shared catch slot C, checked at the flush; k = 6 checks it here.)
     auto ladd = [&](uint32_t id, int d) {
-      if (id >= C) {
+      if (K <= 5) {
+        atomicAdd(&s_hist[min(id, C)], d);
+      } else if (id < C) {
+        atomicAdd(&ghist[id], (unsigned long long)d);
+      } else {
         atomicOr(w.err, kErrStackOverflow);
-        return;
       }
-      if (K <= 5) atomicAdd(&s_hist[id], d);
-      else atomicAdd(&ghist[id], (unsigned long long)d);
     };
     auto leaf_budget = [&](int adds) {
       if (K <= 5) {
@@ -815,19 +818,25 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           // (b) the candidates after the group's first choice; those after
           //     choice g are its leaves, keyed by their word to the first k-2
           //     vertices plus slot g; equal keys of a batch share a table read
+          uint32_t pgs[GS];
+#pragma unroll
+          for (int gg = 0; gg < GS; ++gg) pgs[gg] = __shfl_sync(kFull, Pg, gg);
           for (int b = c + 1; b < e; b += 32) {
             const int i0 = b + lane;
             const bool v0 = i0 < e;
             const int u0 = v0 ? buf[i0] : 0;
             const uint32_t lt = v0 ? (uint32_t)lab[u0] : 0u;
             if (v0) lab[u0] = (LT)(lt & LM);
-            for (int gg = 0; gg < ng; ++gg) {
-              const bool vg = v0 && i0 > c + gg;
-              const uint32_t wd = (lt & LM) | (((lt >> (NB + 2 * gg)) & 3u) << NB);
-              const uint32_t pg = __shfl_sync(kFull, Pg, gg);
-              const unsigned peers = __match_any_sync(kFull, vg ? wd : 0xFFFFFFFFu);
-              if (vg && !(peers & lanes_below))
-                ladd(__ldg(&a.table[pg | (wd << OFF1)]), __popc(peers));
+            const int rel = v0 ? i0 - c : 0;  // candidate is after choice g iff rel > g
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg) {
+              if (gg < ng) {
+                const bool vg = rel > gg;
+                const uint32_t wd = (lt & LM) | ((lt >> (2 * gg)) & (3u << NB));
+                const unsigned peers = __match_any_sync(kFull, vg ? wd : 0xFFFFFFFFu);
+                if (vg && !(peers & lanes_below))
+                  ladd(__ldg(&a.table[pgs[gg] | (wd << OFF1)]), __popc(peers));
+              }
             }
           }
           __syncwarp();
@@ -926,6 +935,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           s_hist[i] = 0;
         }
       }
+      if (tid == 0 && s_hist[C] != 0) {
+        atomicOr(w.err, kErrStackOverflow);
+        s_hist[C] = 0;
+      }
     }
     if (tid == 0) {
       s_idle = 0;
@@ -1000,7 +1013,11 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->split_cost = split_cost;
   p->split_scale = (tuning && tuning->split_scale > 0.0) ? tuning->split_scale : 1.0;
   p->items_factor = tuning ? 5.0 : 1.25;
-  p->cap = (tuning && tuning->stack_cap > 0) ? tuning->stack_cap : (K - 1) * std::max(dmax, 1) + 32;
+  // The stack holds the root's forward list and the exclusive neighbours of the
+  // vertices at positions 1..k-3 (positions k-2 and k-1 are finished in place),
+  // each at most one row: k-2 rows of at most dmax entries.
+  p->cap = (tuning && tuning->stack_cap > 0) ? tuning->stack_cap
+                                             : std::max(K - 2, 1) * std::max(dmax, 1) + 32;
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
   p->comb = tuning && tuning->method == MT_METHOD_CELLS;
@@ -1010,7 +1027,8 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   const size_t cell_bytes =
       p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 384 + 16 : 0;
   const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes + kLevelBytes;
-  const size_t hist_bytes = K <= 5 ? round16((size_t)classes * 4) : 0;
+  // k <= 5: one 32-bit counter per class plus a catch slot for invalid ids
+  const size_t hist_bytes = K <= 5 ? round16(((size_t)classes + 1) * 4) : 0;
   const size_t graph_bytes = round16((size_t)(nmax + 1) * 4) + round16((size_t)p->nu_cap * 4);
   int dev = 0, sms = 0, max_smem = 0;
   MT_CUDA_TRY(cudaGetDevice(&dev));
