@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         if (!COMB && L == K - 2) {
           // Choosing the (k-1)-th vertex finishes its k-sets in place, for up
           // to GS consecutive choices at once (as many as the relation word
-          // has free 2-bit slots, at most 4: 3, 2, 4, 4 for k = 3..6): choice
+          // has free 2-bit slots, at most 5: 3, 2, 5, 4 for k = 3..6): choice
           // g marks its row into slot g above the first k-2 positions' bits,
           // so one pass over the shared candidate tail classifies every
           // choice's leaves.
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             fresh = false;
           }
           // slots left in the relation word above the first k-2 positions
-          constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 4 ? (8 * (int)sizeof(LT) - NB) / 2 : 4;
+          constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 5 ? (8 * (int)sizeof(LT) - NB) / 2 : 5;
           static_assert(COMB || GS >= 2, "at least two slots per relation word");
           const int ng = min(GS, ce - c);
           cur_c = c + ng;
@@ -775,10 +775,12 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             rs_g = (r1 - r0 > 32) ? first_above_p(w.ucol, r0, r1, w.root) : r0;
             len_g = r1 - rs_g;
           }
-          const int q1 = __shfl_sync(kFull, len_g, 0);
-          const int q2 = q1 + __shfl_sync(kFull, len_g, 1);
-          const int q3 = q2 + __shfl_sync(kFull, len_g, 2);
-          const int tot = q3 + __shfl_sync(kFull, len_g, 3);
+          // qs[g] = where choice g's row starts in the concatenation
+          int qs[GS + 1];
+          qs[0] = 0;
+#pragma unroll
+          for (int gg = 0; gg < GS; ++gg) qs[gg + 1] = qs[gg] + __shfl_sync(kFull, len_g, gg);
+          const int tot = qs[GS];
           leaf_budget(ng * (e - c - 1) + tot);
           // (a) the group's rows, concatenated over the lanes: choice g sets
           //     slot g of its neighbours (a 32-bit atomic OR on the word that
@@ -792,13 +794,18 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             uint32_t* lab32 = (uint32_t*)lab;
             for (int b = 0; b < tot; b += 32) {
               const int q = b + lane;
-              const int gg = (q >= q1) + (q >= q2) + (q >= q3);
-              const int rs = __shfl_sync(kFull, rs_g, gg & 3);
-              const uint32_t pg = __shfl_sync(kFull, Pg, gg & 3);
+              int gg = 0, off = 0;
+#pragma unroll
+              for (int t = 1; t < GS; ++t)
+                if (q >= qs[t]) {
+                  gg = t;
+                  off = qs[t];
+                }
+              const int rs = __shfl_sync(kFull, rs_g, gg);
+              const uint32_t pg = __shfl_sync(kFull, Pg, gg);
               bool ex = false;
               uint32_t code = 0;
               if (q < tot) {
-                const int off = gg == 0 ? 0 : (gg == 1 ? q1 : (gg == 2 ? q2 : q3));
                 const uint32_t ent = w.ucol[rs + (q - off)];
                 const int u = (int)(ent & kVertexMask);
                 code = ent >> 30;
@@ -809,7 +816,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                   ex = (old & LM) == 0;
                 }
               }
-              const unsigned peers = __match_any_sync(kFull, ex ? (uint32_t)(gg * 4) + code : 0xFFFFFFFFu);
+              const unsigned peers = __match_any_sync(kFull, ex ? (uint32_t)(gg * 4) + code : 0xFFFFFFFFu);  // (choice, code)
               if (ex && !(peers & lanes_below))
                 ladd(__ldg(&a.table[pg | ((code << NB) << OFF1)]), __popc(peers));
             }
