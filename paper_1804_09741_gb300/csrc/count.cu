@@ -245,10 +245,13 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int32_t* data, int count) 
 
 // Relation words: 2 bits per earlier position.  The first k-2 positions take
 // 2(k-2) bits; the slots above them let several (k-1)-th choices be marked at
-// once: 8 bits for k <= 4 (3 and 2 slots), 16 bits for k = 5, 6 (4 slots each).
-// The cell method needs only two flag bits above them: 8 bits up to k = 5.
+// once: 8 bits for k <= 4 (3 and 2 slots), 16 bits for k = 5 (5 slots), 32 bits
+// for k = 6 (8 slots used).  The cell method needs only two flag bits above
+// them: 8 bits up to k = 5, 16 bits for k = 6.
 template <int K, bool CB>
-using LabT = typename std::conditional<(K <= 4 || (CB && K <= 5)), uint8_t, uint16_t>::type;
+using LabT = typename std::conditional<
+    (K <= 4 || (CB && K <= 5)), uint8_t,
+    typename std::conditional<(K == 5 || CB), uint16_t, uint32_t>::type>::type;
 
 template <typename LT>
 struct WarpCtx {
@@ -735,7 +738,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         if (!COMB && L == K - 2) {
           // Choosing the (k-1)-th vertex finishes its k-sets in place, for up
           // to GS consecutive choices at once (as many as the relation word
-          // has free 2-bit slots, at most 5: 3, 2, 5, 4 for k = 3..6): choice
+          // has free 2-bit slots, at most 8: 3, 2, 5, 8 for k = 3..6): choice
           // g marks its row into slot g above the first k-2 positions' bits,
           // so one pass over the shared candidate tail classifies every
           // choice's leaves.
@@ -761,7 +764,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             fresh = false;
           }
           // slots left in the relation word above the first k-2 positions
-          constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 5 ? (8 * (int)sizeof(LT) - NB) / 2 : 5;
+          constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 8 ? (8 * (int)sizeof(LT) - NB) / 2 : 8;
           static_assert(COMB || GS >= 2, "at least two slots per relation word");
           const int ng = min(GS, ce - c);
           cur_c = c + ng;
@@ -1028,7 +1031,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
   p->comb = tuning && tuning->method == MT_METHOD_CELLS;
-  const size_t lab_elem = (K <= 4 || (p->comb && K <= 5)) ? 1 : 2;
+  const size_t lab_elem = (K <= 4 || (p->comb && K <= 5)) ? 1 : ((K == 5 || p->comb) ? 2 : 4);
   const size_t lab_bytes = round16((size_t)nmax * lab_elem);
   const size_t cells = (size_t)1 << (2 * (K - 2));
   const size_t cell_bytes =
