@@ -119,9 +119,10 @@ mt_status mt_graph_copy_csr(const mt_graph* g, int32_t* row_ptr, int32_t* col, v
  * 2^(k(k-1))/4 bytes of scratch freed before return.
  * Key layout ("extension-order key", used by the counting kernels): the k
  * vertices are listed in the order the enumerator adds them; position p >= 1
- * owns the 2p bits starting at p(p-1), and within them bits 2q and 2q+1
- * (q < p) are set iff the arcs (position q -> position p) and (position p ->
- * position q) exist.  Synchronises `stream`.
+ * owns the 2p bits starting at k(k-1) - p(p+1) (the last position in the
+ * lowest bits), and within them bits 2q and 2q+1 (q < p) are set iff the arcs
+ * (position q -> position p) and (position p -> position q) exist.
+ * Synchronises `stream`.
  * Errors: MT_EUNSUPPORTED (k outside 3..6), MT_ENOMEM, MT_ECUDA. */
 mt_status mt_table_build(int k, void* stream, mt_table** out);
 

@@ -87,6 +87,11 @@ __device__ __forceinline__ float branch_cost(int x1) {
   return 1.f + (float)x1 + choose_f(x1, K - 2) * (K >= 4 ? 2.f : 1.f);
 }
 
+// Offset of position p's 2p bits in an extension-order key of k vertices:
+// later positions sit lower, so the k-sets below one (k-2)-set differ only in
+// the low bits of their keys and read nearby table slots.
+__host__ __device__ constexpr int key_off(int k, int p) { return k * (k - 1) - p * (p + 1); }
+
 // Whether vertex x is in sorted packed entries [lo, hi).
 __device__ __forceinline__ bool contains(const uint32_t* __restrict__ ucol, int lo, int hi, int x) {
   while (lo < hi) {
@@ -362,6 +367,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   const int nwarps = blockDim.x >> 5;
   const unsigned lanes_below = (1u << lane) - 1u;
   int since = 0;  // this warp's enumeration adds since its last flush
+  bool bad_id = false;  // k = 6: a table read gave an id out of range
   unsigned char* sp = smem;
   int32_t* s_urow = (int32_t*)sp;
   uint32_t* s_ucol = (uint32_t*)(sp + (GC ? ((a.nmax + 1) * 4 + 15) / 16 * 16 : 0));
@@ -480,14 +486,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     // (adds of other warps stay in the counters).  A counter then never holds
     // more than warps x (kLeafBudget + one choice's adds) < 2^31.
     // (An id out of range, which a valid table never holds, lands in the
-    // shared catch slot C, checked at the flush; k = 6 checks it here.)
+    // shared catch slot C, checked at the flush; for k = 6 it adds nothing and
+    // is recorded in `bad_id`, reported when the thread exits.  Neither form
+    // branches on the table read, so the reads of several slots overlap.)
     auto ladd = [&](uint32_t id, int d) {
       if (K <= 5) {
         atomicAdd(&s_hist[min(id, C)], d);
-      } else if (id < C) {
-        atomicAdd(&ghist[id], (unsigned long long)d);
       } else {
-        atomicOr(w.err, kErrStackOverflow);
+        const bool ok = id < C;
+        bad_id |= !ok;
+        atomicAdd(&ghist[ok ? id : 0u], ok ? (unsigned long long)d : 0ull);
       }
     };
     auto leaf_budget = [&](int adds) {
@@ -515,7 +523,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       constexpr int NB = 2 * (K - 2);
       constexpr uint32_t LM = (1u << NB) - 1u;
       constexpr uint32_t INC = 1u << NB, INT = 2u << NB;
-      constexpr int OFF2 = (K - 2) * (K - 3), OFF1 = (K - 1) * (K - 2);
+      constexpr int OFF2 = key_off(K, K - 2), OFF1 = key_off(K, K - 1);
       // 1. cells of the choices and of the tail; flag E's members
       for (int b = c; b < e; b += 32) {
         const int i = b + lane;
@@ -749,8 +757,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           }
           constexpr int NB = 2 * (K - 2);
           constexpr uint32_t LM = (1u << NB) - 1u;
-          constexpr int OFF1 = (K - 1) * (K - 2);
-          constexpr int OFF2 = (K - 2) * (K - 3);
+          constexpr int OFF1 = key_off(K, K - 1);
+          constexpr int OFF2 = key_off(K, K - 2);
           if (fresh) {
             // a new candidate list: clear slot codes left by earlier rows
             for (int b = c; b < e; b += 32) {
@@ -901,7 +909,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             }
           }
           const int x = buf[c];
-          const uint32_t nkey = key | (((uint32_t)lab[x] & ((1u << (2 * L)) - 1u)) << (L * (L - 1)));
+          const uint32_t nkey = key | (((uint32_t)lab[x] & ((1u << (2 * L)) - 1u)) << key_off(K, L));
           const int ne = push_vertex(w, x, L, e, (1u << (2 * (K - 2))) - 1u);
           if (lane == 0) {
             int* sv = lvs + 5 * L;
@@ -967,6 +975,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     __syncthreads();
     g = s_cur_g;
   }
+  if (bad_id) atomicOr(&a.hdr->err, kErrStackOverflow);
 }
 
 // ------------------------------------------------------------------ host side

@@ -1,8 +1,9 @@
 // K1: the isomorphism table ISO of Sec. 3.2, built on the device.
 //
 // Keys are "extension-order keys": position p >= 1 of the enumerated vertex
-// sequence owns bits [p(p-1), p(p+1)); inside them bits 2q / 2q+1 (q < p) say
-// whether the arcs q->p / p->q exist.  For every key the builder
+// sequence owns the 2p bits starting at k(k-1) - p(p+1) (the last position
+// lowest); inside them bits 2q / 2q+1 (q < p) say whether the arcs q->p /
+// p->q exist.  For every key the builder
 //  1. expands it to an 8x8 bit matrix (row i in byte i, column j in bit j),
 //  2. walks all k! orderings of the vertices by adjacent transpositions
 //     (Steinhaus-Johnson-Trotter order; each step swaps two neighbouring rows
@@ -60,7 +61,7 @@ static std::vector<uint8_t> sjt_sequence(int k) {
 __device__ __forceinline__ uint64_t key_to_matrix(uint32_t key, int k) {
   uint64_t x = 0;
   for (int p = 1; p < k; ++p) {
-    const int off = p * (p - 1);
+    const int off = k * (k - 1) - p * (p + 1);
     for (int q = 0; q < p; ++q) {
       if ((key >> (off + 2 * q)) & 1u) x |= 1ull << (8 * q + p);      // q -> p
       if ((key >> (off + 2 * q + 1)) & 1u) x |= 1ull << (8 * p + q);  // p -> q

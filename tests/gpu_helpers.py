@@ -10,7 +10,7 @@ def ext_key_to_mask(k: int, keys: np.ndarray) -> np.ndarray:
     keys = np.asarray(keys, dtype=np.uint64)
     out = np.zeros(keys.shape, dtype=np.uint64)
     for p in range(1, k):
-        off = p * (p - 1)
+        off = k * (k - 1) - p * (p + 1)
         for q in range(p):
             fwd = (keys >> np.uint64(off + 2 * q)) & np.uint64(1)      # q -> p
             back = (keys >> np.uint64(off + 2 * q + 1)) & np.uint64(1)  # p -> q
