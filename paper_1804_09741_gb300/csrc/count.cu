@@ -92,6 +92,17 @@ __device__ __forceinline__ float branch_cost(int x1) {
 // the low bits of their keys and read nearby table slots.
 __host__ __device__ constexpr int key_off(int k, int p) { return k * (k - 1) - p * (p + 1); }
 
+// Histogram reductions without a returned value (PTX red): the issuing warp
+// never waits for them.
+__device__ __forceinline__ void red_add_global(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v)
+               : "memory");
+}
+__device__ __forceinline__ void red_add_shared(int* p, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v)
+               : "memory");
+}
+
 // Whether vertex x is in sorted packed entries [lo, hi).
 __device__ __forceinline__ bool contains(const uint32_t* __restrict__ ucol, int lo, int hi, int x) {
   while (lo < hi) {
@@ -491,11 +502,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
     // branches on the table read, so the reads of several slots overlap.)
     auto ladd = [&](uint32_t id, int d) {
       if (K <= 5) {
-        atomicAdd(&s_hist[min(id, C)], d);
+        red_add_shared(&s_hist[min(id, C)], d);
       } else {
         const bool ok = id < C;
         bad_id |= !ok;
-        atomicAdd(&ghist[ok ? id : 0u], ok ? (unsigned long long)d : 0ull);
+        red_add_global(&ghist[ok ? id : 0u], ok ? (unsigned long long)d : 0ull);
       }
     };
     auto leaf_budget = [&](int adds) {
