@@ -538,8 +538,28 @@ def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0):
     ok = all(r[0] == 2 for r in res)
     sub = sum(int(r[1].sum()) for r in res if r[1] is not None)
     srv.free()
+    # the plain path on the same requests: load, one count launch, histogram
+    # back to the host, one request after another
+    def plain(k, g):
+        dg = mt.graph_from(g)
+        if method:
+            h = mt.to_numpy_u64(mt.count_tuned(dg, tables[k], method=method))
+        else:
+            h = mt.count_host(dg, tables[k])
+        dg.free()
+        return h
+    for k, g in reqs[:4]:
+        plain(k, g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_ok = True
+    for (k, g), r in zip(reqs, res):
+        plain_ok &= r[1] is not None and np.array_equal(plain(k, g), r[1])
+    plain_wall = time.perf_counter() - t0
     ks = [k for k, _ in reqs]
     return {"graphs_per_s": num / wall2, "capacity_graphs_per_s": cap,
+            "plain_graphs_per_s": num / plain_wall, "served_over_plain": plain_wall / wall,
+            "plain_equal": bool(plain_ok),
             "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "subgraphs_per_s": sub / wall2,
             "requests": num, "k_mix": {str(k): ks.count(k) for k in (3, 4, 5, 6)},
