@@ -480,13 +480,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
         const long long now = (long long)old + d;
         if (old < (1 << 29) && now >= (1 << 29)) {
           atomicSub(&s_hist[id], 1 << 29);
-          atomicAdd(&ghist[id], 1ull << 29);
+          red_add_global(&ghist[id], 1ull << 29);
         } else if (old > -(1 << 29) && now <= -(1 << 29)) {
           atomicAdd(&s_hist[id], 1 << 29);
-          atomicAdd(&ghist[id], (unsigned long long)(-(1ll << 29)));
+          red_add_global(&ghist[id], (unsigned long long)(-(1ll << 29)));
         }
       } else {
-        atomicAdd(&ghist[id], (unsigned long long)delta);
+        red_add_global(&ghist[id], (unsigned long long)delta);
       }
     };
 
