@@ -520,7 +520,7 @@ def serving_requests(num, seed):
     return out
 
 
-def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0):
+def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0, round_cost=1.6e9):
     """Continuous-batching server on a seeded stream of mixed-k requests:
     closed-loop capacity first, then Poisson arrivals at 80% of it."""
     from paper_1804_09741_gb300.server import Server, poisson_arrivals, run_stream
@@ -529,7 +529,7 @@ def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0):
     for k in (3, 4, 5, 6):
         if k not in tables:
             tables[k] = mt.table_build(k)
-    srv = Server(tables, memory_budget=16 << 30, max_slots=32, round_cost=4e8, method=method)
+    srv = Server(tables, memory_budget=16 << 30, max_slots=32, round_cost=round_cost, method=method)
     run_stream(srv, reqs[:4])  # warm-up
     res, lat, wall = run_stream(srv, reqs)
     cap = num / wall
@@ -562,7 +562,8 @@ def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0):
             "plain_equal": bool(plain_ok),
             "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "subgraphs_per_s": sub / wall2,
-            "requests": num, "k_mix": {str(k): ks.count(k) for k in (3, 4, 5, 6)},
+            "requests": num, "round_cost": round_cost,
+            "k_mix": {str(k): ks.count(k) for k in (3, 4, 5, 6)},
             "n_range": [int(min(g.n for _, g in reqs)), int(max(g.n for _, g in reqs))],
             "all_ok": ok, "method": "cells" if method else "enumerate"}
 

@@ -328,9 +328,11 @@ mt_status mt_probe_rates(uint64_t table_words, uint64_t hist_words, double* gath
  * `memory_budget` bytes.  Work runs in rounds: each round gives every active
  * request a root range whose estimated cost is its share of `round_cost`
  * (estimated k-subgraphs; a k-set belongs to its smallest vertex, so the
- * ranges of one request never overlap) and launches one enumeration per k over
- * all requests' ranges.  A request that arrives while a round runs joins the
- * next round.  The server owns two CUDA streams; one host thread drives it. */
+ * ranges of one request never overlap; shares are water-filled, so a request
+ * needing less than an equal share finishes and the rest goes to the others)
+ * and launches one enumeration per k over all requests' ranges, each k on its
+ * own stream.  A request that arrives while a round runs joins the next round.
+ * The server owns six CUDA streams; one host thread drives it. */
 mt_status mt_server_create(const mt_table* t3, const mt_table* t4, const mt_table* t5,
                            const mt_table* t6, size_t memory_budget, int max_slots,
                            double round_cost, mt_server** out);

@@ -9,7 +9,11 @@
 //  * a round gives every active request a chunk of its roots (a root range
 //    whose estimated cost fits the request's share of the round budget; a
 //    connected k-set belongs to its smallest vertex, so chunks never overlap)
-//    and launches one planner + enumerator per k over all chunks of that k;
+//    and launches one planner + enumerator per k over all chunks of that k.
+//    Shares are water-filled: a request that needs less than an equal share
+//    finishes, and what it leaves goes to the others.  The k's launches of a
+//    round run on their own streams, so one k's kernel tail overlaps the
+//    next k's kernel;
 //  * a request whose last chunk ran is complete when its round's event fires:
 //    its histogram was copied to a pinned buffer behind the kernels, its device
 //    memory goes back to the pool and its slot frees up for the next admission.
@@ -60,6 +64,8 @@ struct mt_server {
   double round_cost = 0;
   cudaStream_t stream = nullptr, load_stream = nullptr;
   cudaEvent_t load_ev = nullptr;
+  cudaStream_t kstream[4] = {nullptr, nullptr, nullptr, nullptr};  // a round's launch per k
+  cudaEvent_t fork_ev = nullptr, kdone_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::deque<mt::SrvRequest*> pending;
   std::vector<mt::SrvRequest*> active;
   std::map<uint64_t, mt::SrvRequest*> all;
@@ -224,18 +230,37 @@ static mt_status step(mt_server* s, int32_t* completed) {
   for (SrvRequest* r : s->active)
     if (r->next_root < r->n) open.push_back(r);
   if (!open.empty()) {
-    const double share = s->round_cost / (double)open.size();
+    // water-filling: in ascending order of remaining cost, each request takes
+    // the smaller of its remaining cost and an equal share of what is left
+    std::vector<double> rem(open.size()), give(open.size());
+    std::vector<size_t> order(open.size());
+    for (size_t i = 0; i < open.size(); ++i) {
+      rem[i] = open[i]->cum[open[i]->n] - open[i]->cum[open[i]->next_root];
+      order[i] = i;
+    }
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return rem[x] < rem[y]; });
+    double budget = s->round_cost;
+    size_t left = open.size();
+    for (size_t i : order) {
+      give[i] = std::min(rem[i], budget / (double)left);
+      budget -= give[i];
+      --left;
+    }
     struct Chunk {
       SrvRequest* r;
       int a, b;
     };
     std::vector<Chunk> by_k[4];
-    for (SrvRequest* r : open) {
+    for (size_t i = 0; i < open.size(); ++i) {
+      SrvRequest* r = open[i];
       const int a = r->next_root;
-      const double limit = r->cum[a] + share;
-      int b = (int)(std::upper_bound(r->cum.begin() + a + 1, r->cum.end(), limit) - r->cum.begin()) - 1;
-      b = std::max(b, a + 1);
-      b = std::min(b, r->n);
+      int b = r->n;
+      if (give[i] < rem[i]) {
+        const double limit = r->cum[a] + give[i];
+        b = (int)(std::upper_bound(r->cum.begin() + a + 1, r->cum.end(), limit) - r->cum.begin()) - 1;
+        b = std::max(b, a + 1);
+        b = std::min(b, r->n);
+      }
       by_k[r->k - 3].push_back({r, a, b});
       r->next_root = b;
       if (b == r->n) R.finishing.push_back(r);
@@ -250,6 +275,8 @@ static mt_status step(mt_server* s, int32_t* completed) {
       R.h_cap = std::max<size_t>(total, 64);
     }
     size_t off = 0;
+    CountPlan plans[4];
+    int nmaxs[4] = {0, 0, 0, 0};
     for (int ki = 0; ki < 4; ++ki) {
       auto& chunks = by_k[ki];
       if (chunks.empty()) continue;
@@ -282,8 +309,20 @@ static mt_status step(mt_server* s, int32_t* completed) {
       }
       MT_CUDA_TRY(cudaMemcpyAsync(s->d_graphs[ki], hg, chunks.size() * sizeof(DevGraph),
                                   cudaMemcpyHostToDevice, s->stream));
-      MT_TRY(count_enqueue(p, s->ws[ki], s->d_graphs[ki], table_device(t), 0, nmax, s->stream));
+      plans[ki] = p;
+      nmaxs[ki] = nmax;
       off += chunks.size();
+    }
+    // fork: each k's launch waits for what the main stream holds (loads,
+    // allocations, descriptors, the previous round), then joins back
+    MT_CUDA_TRY(cudaEventRecord(s->fork_ev, s->stream));
+    for (int ki = 0; ki < 4; ++ki) {
+      if (by_k[ki].empty()) continue;
+      MT_CUDA_TRY(cudaStreamWaitEvent(s->kstream[ki], s->fork_ev, 0));
+      MT_TRY(count_enqueue(plans[ki], s->ws[ki], s->d_graphs[ki], table_device(s->tables[ki]), 0,
+                           nmaxs[ki], s->kstream[ki]));
+      MT_CUDA_TRY(cudaEventRecord(s->kdone_ev[ki], s->kstream[ki]));
+      MT_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->kdone_ev[ki], 0));
     }
     for (SrvRequest* r : R.finishing) {
       const uint32_t C = table_classes(s->tables[r->k - 3]);
@@ -325,6 +364,11 @@ mt_status mt_server_create(const mt_table* t3, const mt_table* t4, const mt_tabl
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->load_ev, cudaEventDisableTiming);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&s->rb[i].ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&s->kstream[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kdone_ev[i], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));
     mt_server_free(s);
@@ -423,6 +467,14 @@ mt_status mt_server_free(mt_server* s) {
     if (b.h_graphs) cudaFreeHost(b.h_graphs);
   }
   if (s->load_ev) cudaEventDestroy(s->load_ev);
+  if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+  for (int i = 0; i < 4; ++i) {
+    if (s->kstream[i]) {
+      cudaStreamSynchronize(s->kstream[i]);
+      cudaStreamDestroy(s->kstream[i]);
+    }
+    if (s->kdone_ev[i]) cudaEventDestroy(s->kdone_ev[i]);
+  }
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->load_stream) cudaStreamDestroy(s->load_stream);
   delete s;

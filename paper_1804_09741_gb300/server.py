@@ -17,7 +17,7 @@ class Server:
     """Continuous-batching server over resident per-k tables."""
 
     def __init__(self, tables: dict, memory_budget: int = 8 << 30, max_slots: int = 64,
-                 round_cost: float = 4e8, method: int = 0):
+                 round_cost: float = 1.6e9, method: int = 0):
         self.lib = load_library()
         self.tables = dict(tables)
         ts = [self.tables[k].handle if k in self.tables else None for k in (3, 4, 5, 6)]
