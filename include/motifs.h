@@ -126,6 +126,28 @@ mt_status mt_graph_copy_csr(const mt_graph* g, int32_t* row_ptr, int32_t* col, v
  * Errors: MT_EUNSUPPORTED (k outside 3..6), MT_ENOMEM, MT_ECUDA. */
 mt_status mt_table_build(int k, void* stream, mt_table** out);
 
+/* The k = 6 table in compact form (the paper's isomorphism table, Sec. 3.2,
+ * has one slot per key; it has no compact form): 199 x 2^18 uint32 slots
+ * (208 MB) instead of 2^30 (4 GiB), plus a
+ * 4096-entry prefix-class array and 4096 x 256 bytes of word relabellings.
+ * A 6-vertex key splits into its first four vertices X (key bits 18..29), the
+ * fifth vertex's word (bits 10..17) and the sixth's (bits 0..9).  X is mapped
+ * to one of the 199 weakly connected 4-vertex classes by relabelling it into
+ * that class's canonical order; the two words are relabelled with it (their
+ * fields for the vertices of X are permuted, the sixth vertex's field for the
+ * fifth is not), which leaves the class of the whole unchanged.  Slot
+ * (class of X) << 18 | relabelled fifth word << 10 | relabelled sixth word
+ * holds the dense id.  Built from the full table, which is freed before return
+ * (peak device memory: the full table's).  Class ids and class masks are the
+ * full table's.  Counting with a compact table supports the per-subgraph
+ * method only (MT_METHOD_CELLS gives MT_EUNSUPPORTED); mt_table_entries reads
+ * compact slots.  Synchronises `stream`.
+ * Errors: MT_EUNSUPPORTED (k != 6), MT_ENOMEM, MT_ECUDA. */
+mt_status mt_table_build_compact(int k, void* stream, mt_table** out);
+
+/* *compact = 1 for a table from mt_table_build_compact, else 0. */
+mt_status mt_table_is_compact(const mt_table* t, int* compact);
+
 mt_status mt_table_free(mt_table* t);
 
 /* k of the table and the number of weakly connected classes C. */
@@ -137,8 +159,9 @@ mt_status mt_table_num_classes(const mt_table* t, uint32_t* out);
 mt_status mt_table_class_masks(const mt_table* t, uint32_t* masks);
 
 /* Copy table slots [first, first+count) (extension-order keys) to a HOST array
- * of uint32 dense ids (0xFFFFFFFF = disconnected).  Synchronous.
- * Errors: MT_EINVAL when the range leaves [0, 2^(k(k-1))). */
+ * of uint32 dense ids (0xFFFFFFFF = disconnected).  Synchronous.  For a compact
+ * table the slots are its 199 x 2^18 compact slots.
+ * Errors: MT_EINVAL when the range leaves the table's slots. */
 mt_status mt_table_entries(const mt_table* t, uint64_t first, uint64_t count, uint32_t* ids);
 
 /* ----------------------------------------------------------------- counting */

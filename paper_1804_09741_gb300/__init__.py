@@ -52,6 +52,8 @@ SIGNATURES = {
     "mt_graph_info": (ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     "mt_graph_copy_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_table_build": (ctypes.c_int, [ctypes.c_int, _vp, _P(_vp)]),
+    "mt_table_build_compact": (ctypes.c_int, [ctypes.c_int, _vp, _P(_vp)]),
+    "mt_table_is_compact": (ctypes.c_int, [_vp, _P(ctypes.c_int)]),
     "mt_table_free": (ctypes.c_int, [_vp]),
     "mt_table_k": (ctypes.c_int, [_vp, _P(ctypes.c_int)]),
     "mt_table_num_classes": (ctypes.c_int, [_vp, _P(_u32)]),
@@ -200,6 +202,9 @@ class Table:
         _check(_lib.mt_table_k(handle, ctypes.byref(k)), "mt_table_k")
         _check(_lib.mt_table_num_classes(handle, ctypes.byref(c)), "mt_table_num_classes")
         self.k, self.num_classes = k.value, c.value
+        cp = ctypes.c_int()
+        _check(_lib.mt_table_is_compact(handle, ctypes.byref(cp)), "mt_table_is_compact")
+        self.compact = bool(cp.value)
         self._masks = None
 
     def class_masks(self) -> np.ndarray:
@@ -226,10 +231,15 @@ class Table:
             pass
 
 
-def table_build(k: int, stream=None) -> Table:
+def table_build(k: int, stream=None, compact: bool = False) -> Table:
+    """mt_table_build, or mt_table_build_compact (k = 6 only) with `compact`."""
     load_library()
     h = _vp()
-    _check(_lib.mt_table_build(k, _stream(stream), ctypes.byref(h)), "mt_table_build")
+    if compact:
+        _check(_lib.mt_table_build_compact(k, _stream(stream), ctypes.byref(h)),
+               "mt_table_build_compact")
+    else:
+        _check(_lib.mt_table_build(k, _stream(stream), ctypes.byref(h)), "mt_table_build")
     return Table(h.value)
 
 

@@ -113,7 +113,7 @@ static mt_status batch_create(const mt_graph* g0, const mt_table* t, int R, uint
   b->null_model = null_model;
   mt_status st = count_configure_tuned(&b->plan, K, R + 1, n, dbound,
                                        (int64_t)(R + 1) * std::max(m, 1),
-                                       2 * (int64_t)std::max(m, 1), C, tuning);
+                                       2 * (int64_t)std::max(m, 1), C, tuning, table_compact(t));
   if (st != MT_OK) {
     delete b;
     return st;
@@ -233,7 +233,7 @@ static mt_status batch_enqueue(mt_batch* b, cudaStream_t s) {
   MT_CUDA_TRY(cudaGetLastError());
   MT_CUDA_TRY(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
   MT_CUDA_TRY(cudaMemsetAsync(b->d_hists, 0, (size_t)(R + 1) * b->C * 8, s));
-  if (n >= b->K) MT_TRY(count_enqueue(b->plan, b->ws, b->d_graphs, table_device(b->t), 0, n, s));
+  if (n >= b->K) MT_TRY(count_enqueue(b->plan, b->ws, b->d_graphs, table_view(b->t), 0, n, s));
   MT_CUDA_TRY(cudaEventRecordWithFlags(b->ev[2], s, cudaEventRecordExternal));
   k_zscore<<<(b->C + 255) / 256, 256, 0, s>>>(b->d_hists, R, b->C, b->d_z);
   MT_CUDA_TRY(cudaGetLastError());

@@ -54,6 +54,15 @@ struct Item {
 };
 static_assert(sizeof(Item) == 16, "Item is 16 bytes");
 
+// What a counting launch reads of a table: the slots, and for the compact
+// k = 6 form (xclass != nullptr) the class of each 4-vertex prefix key and its
+// word relabelling (4096 x 256 bytes).
+struct TableView {
+  const uint32_t* slots = nullptr;
+  const uint16_t* xclass = nullptr;
+  const uint8_t* xmap = nullptr;
+};
+
 // Record one CUDA error text for mt_last_error().
 void set_last_error(const std::string& s);
 

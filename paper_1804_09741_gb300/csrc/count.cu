@@ -350,10 +350,12 @@ struct CountArgs {
   uint32_t* qhead;           // per-graph queue heads
   Hdr* hdr;
   const uint32_t* table;
+  const uint16_t* xclass;    // compact k = 6 table: prefix key -> class of the first 4 vertices
+  const uint8_t* xmap;       //   and its word relabelling (256 bytes per prefix key)
   void* lab_global;
   int G, nmax, nu_cap, cap;
   uint32_t classes;
-  int graph_bytes, hist_bytes, lab_bytes, buf_bytes, cell_bytes;
+  int graph_bytes, hist_bytes, lab_bytes, buf_bytes, cell_bytes, map_bytes;
 };
 
 // Cells of the last two positions (combinatorial counting): a relation word to
@@ -387,8 +389,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   sp += a.hist_bytes;
   unsigned char* mine =
       sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0) +
-                          kLevelBytes);
+                          kLevelBytes + a.map_bytes);
   int* lvs = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
+  // compact k = 6 table: the current 4-vertex prefix's word relabelling
+  uint8_t* xmw = (uint8_t*)lvs + kLevelBytes;
+  const bool cpt = K == 6 && !COMB && a.xclass != nullptr;
   using LT = LabT<K, COMB>;
   // each warp's relation words start on a 16-byte boundary (lab_bytes is a
   // multiple of 16), so 32-bit atomics on them are aligned
@@ -735,6 +740,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
       // without them, and a candidate list is cleaned once when its level
       // (k-2 positions chosen) is entered; every other reader masks them.
       bool fresh = true;
+      uint32_t xpre = 0;  // compact table: class of the current 4-vertex prefix, in place
       int L = 1;
       auto pop_level = [&]() {
         L -= 1;
@@ -781,6 +787,19 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             }
             __syncwarp();
             fresh = false;
+            if (cpt) {
+              // class of the first four vertices and the relabelling of words
+              // to their canonical order (positions 1..3 sit in key bits 18..29)
+              const uint32_t xk = key >> 18;
+              ((uint2*)xmw)[lane] = __ldg((const uint2*)(a.xmap + (size_t)xk * 256) + lane);
+              uint32_t c4 = __ldg(&a.xclass[xk]);
+              if (c4 >= 199u) {  // a disconnected prefix, which the enumeration never forms
+                atomicOr(w.err, kErrStackOverflow);
+                c4 = 0;
+              }
+              xpre = c4 << 18;
+              __syncwarp();
+            }
           }
           // slots left in the relation word above the first k-2 positions
           constexpr int GS = (8 * (int)sizeof(LT) - NB) / 2 < 8 ? (8 * (int)sizeof(LT) - NB) / 2 : 8;
@@ -792,7 +811,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           int rs_g = 0, len_g = 0;
           if (lane < ng) {
             const int y = buf[c + lane];
-            Pg = key | ((uint32_t)(lab[y] & LM) << OFF2);
+            Pg = cpt ? xpre | ((uint32_t)xmw[(uint32_t)lab[y] & LM] << OFF2)
+                     : key | ((uint32_t)(lab[y] & LM) << OFF2);
             const int r0 = w.urow[y], r1 = w.urow[y + 1];
             rs_g = (r1 - r0 > 32) ? first_above_p(w.ucol, r0, r1, w.root) : r0;
             len_g = r1 - rs_g;
@@ -857,11 +877,12 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             const uint32_t lt = v0 ? (uint32_t)lab[u0] : 0u;
             if (v0) lab[u0] = (LT)(lt & LM);
             const int rel = v0 ? i0 - c : 0;  // candidate is after choice g iff rel > g
+            const uint32_t lb = cpt ? (uint32_t)xmw[lt & LM] : (lt & LM);
 #pragma unroll
             for (int gg = 0; gg < GS; ++gg) {
               if (gg < ng) {
                 const bool vg = rel > gg;
-                const uint32_t wd = (lt & LM) | ((lt >> (2 * gg)) & (3u << NB));
+                const uint32_t wd = lb | ((lt >> (2 * gg)) & (3u << NB));
                 const unsigned peers = __match_any_sync(kFull, vg ? wd : 0xFFFFFFFFu);
                 if (vg && !(peers & lanes_below))
                   ladd(__ldg(&a.table[pgs[gg] | (wd << OFF1)]), __popc(peers));
@@ -1015,7 +1036,7 @@ static const void* pick_kernel(int K, bool gc, bool ls, bool cb) {
 
 mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
                           int64_t entry_stride, uint32_t classes, double split_cost,
-                          int warps_per_block) {
+                          int warps_per_block, bool compact) {
   mt_tuning t;
   t.split_cost = split_cost;
   t.split_scale = 0.0;
@@ -1024,12 +1045,13 @@ mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_
   t.method = MT_METHOD_ENUMERATE;
   const bool plain = split_cost == 0.0;
   MT_TRY(count_configure_tuned(p, K, G, nmax, dmax, fwd_bound, entry_stride, classes,
-                               plain && warps_per_block == 0 ? nullptr : &t));
+                               plain && warps_per_block == 0 ? nullptr : &t, compact));
   return MT_OK;
 }
 
 mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
-                                int64_t entry_stride, uint32_t classes, const mt_tuning* tuning) {
+                                int64_t entry_stride, uint32_t classes, const mt_tuning* tuning,
+                                bool compact) {
   if (K < 3 || K > 6 || G < 1 || nmax < 1) return MT_EINVAL;
   const double split_cost = tuning ? tuning->split_cost : 0.0;
   const int warps_per_block = tuning ? tuning->warps_per_block : 0;
@@ -1051,12 +1073,15 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   if (p->cap > 65535) return MT_EUNSUPPORTED;
   p->nu_cap = (int)p->entry_stride;
   p->comb = tuning && tuning->method == MT_METHOD_CELLS;
+  p->compact = compact;
+  if (compact && (K != 6 || p->comb)) return MT_EUNSUPPORTED;
+  p->map_bytes = compact ? 256 : 0;
   const size_t lab_elem = (K <= 4 || (p->comb && K <= 5)) ? 1 : ((K == 5 || p->comb) ? 2 : 4);
   const size_t lab_bytes = round16((size_t)nmax * lab_elem);
   const size_t cells = (size_t)1 << (2 * (K - 2));
   const size_t cell_bytes =
       p->comb ? round16(cells * 4) + round16(std::min<size_t>(cells, p->cap) * 2) + 384 + 16 : 0;
-  const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes + kLevelBytes;
+  const size_t buf_bytes = round16((size_t)p->cap * 2) + cell_bytes + kLevelBytes + p->map_bytes;
   // k <= 5: one 32-bit counter per class plus a catch slot for invalid ids
   const size_t hist_bytes = K <= 5 ? round16(((size_t)classes + 1) * 4) : 0;
   const size_t graph_bytes = round16((size_t)(nmax + 1) * 4) + round16((size_t)p->nu_cap * 4);
@@ -1096,7 +1121,7 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->graph_bytes = p->gcache ? graph_bytes : 0;
   p->hist_bytes = hist_bytes;
   p->lab_bytes = lab_bytes;
-  p->buf_bytes = buf_bytes - cell_bytes - kLevelBytes;
+  p->buf_bytes = buf_bytes - cell_bytes - kLevelBytes - p->map_bytes;
   p->cell_bytes = cell_bytes;
   const void* kern = pick_kernel(K, p->gcache, p->lab_smem, p->comb);
   MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1141,7 +1166,7 @@ static void launch_count(const CountPlan& p, const CountArgs& a, unsigned thread
 
 template <int K>
 static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graphs,
-                             const uint32_t* table, int32_t rb, int32_t re, cudaStream_t s) {
+                             const TableView& table, int32_t rb, int32_t re, cudaStream_t s) {
   char* base = (char*)ws;
   Hdr* hdr = (Hdr*)(base + p.off_hdr);
   uint32_t* qhead = (uint32_t*)(base + p.off_qhead);
@@ -1176,7 +1201,10 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
   a.item_off = cnt;
   a.qhead = qhead;
   a.hdr = hdr;
-  a.table = table;
+  a.table = table.slots;
+  a.xclass = p.compact ? table.xclass : nullptr;
+  a.xmap = p.compact ? table.xmap : nullptr;
+  a.map_bytes = (int)p.map_bytes;
   a.lab_global = lab;
   a.G = p.G;
   a.nmax = p.nmax;
@@ -1195,7 +1223,7 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
 }
 
 mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
-                        const uint32_t* table, int32_t root_begin, int32_t root_end,
+                        const TableView& table, int32_t root_begin, int32_t root_end,
                         cudaStream_t s) {
   cudaError_t e;
   switch (p.K) {
@@ -1219,7 +1247,7 @@ static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist
   const uint32_t C = table_classes(t);
   CountPlan p;
   MT_TRY(count_configure_tuned(&p, K, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1), C,
-                               tuning));
+                               tuning, table_compact(t)));
   // workspace: plan scratch + the DevGraph + a device histogram
   const size_t extra = 256 + round16((size_t)C * 8);
   const size_t need = p.ws_bytes + extra;
@@ -1251,7 +1279,7 @@ static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist
   MT_CUDA_TRY(cudaMemsetAsync(dh, 0, (size_t)C * 8, s));
   if (g->n >= K && rb < re) {
     MT_CUDA_TRY(cudaEventRecord(g->ev0, s));
-    MT_TRY(count_enqueue(p, g->ws, dg, table_device(t), rb, re, s));
+    MT_TRY(count_enqueue(p, g->ws, dg, table_view(t), rb, re, s));
     MT_CUDA_TRY(cudaEventRecord(g->ev1, s));
   } else {
     MT_CUDA_TRY(cudaEventRecord(g->ev0, s));

@@ -8,6 +8,8 @@ namespace mt {
 const uint32_t* table_device(const mt_table* t);
 int table_k(const mt_table* t);
 uint32_t table_classes(const mt_table* t);
+TableView table_view(const mt_table* t);
+bool table_compact(const mt_table* t);
 
 // Host-side shape of one counting launch over G graphs.
 struct CountPlan {
@@ -24,6 +26,8 @@ struct CountPlan {
   int nu_cap = 0;            // capacity of that copy (undirected entries)
   size_t graph_bytes = 0, hist_bytes = 0, lab_bytes = 0, buf_bytes = 0, cell_bytes = 0;
   bool comb = false;         // count the last two positions by cells (Algorithm 1)
+  bool compact = false;      // the table is the compact k = 6 form
+  size_t map_bytes = 0;      // per-warp word relabelling (compact form)
   int cap = 0;              // stack entries per warp
   size_t smem_bytes = 0;
   uint64_t items_max = 0;
@@ -40,17 +44,20 @@ struct CountPlan {
 // the total number of forward entries (sum of undirected edges) of the G graphs.
 mt_status count_configure(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
                           int64_t entry_stride, uint32_t classes, double split_cost,
-                          int warps_per_block);
+                          int warps_per_block, bool compact = false);
 
 // Same, with the tuning of include/motifs.h (nullptr = automatic).
+// `compact`: the table is the compact k = 6 form (per-subgraph method only;
+// MT_EUNSUPPORTED otherwise).
 mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, int64_t fwd_bound,
-                                int64_t entry_stride, uint32_t classes, const mt_tuning* tuning);
+                                int64_t entry_stride, uint32_t classes, const mt_tuning* tuning,
+                                bool compact = false);
 
 // Enqueue planner + enumerator.  `graphs` is a device array of G DevGraph whose
 // hist pointers are already zeroed (the launch adds into them).  Roots in
 // [root_begin, root_end) only.  No host synchronisation, no allocation.
 mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
-                        const uint32_t* table, int32_t root_begin, int32_t root_end,
+                        const TableView& table, int32_t root_begin, int32_t root_end,
                         cudaStream_t s);
 
 // Read the launch's error word and item count from the workspace (device

@@ -67,7 +67,8 @@ static mt_status count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* h
   const int K = table_k(t);
   const uint32_t C = table_classes(t);
   CountPlan p;
-  MT_TRY(count_configure(&p, K, 1, g->n, g->dmax, g->nu / 2 + 1, g->nu > 0 ? g->nu : 1, C, 0.0, 0));
+  MT_TRY(count_configure(&p, K, 1, g->n, g->dmax, g->nu / 2 + 1, g->nu > 0 ? g->nu : 1, C, 0.0, 0,
+                         table_compact(t)));
   const size_t desc_off = (p.ws_bytes + 255) & ~(size_t)255;
   const size_t need = desc_off + 256;
   if (need > kNoAllocScratchBytes) {
@@ -80,7 +81,7 @@ static mt_status count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* h
   k_put_graph<<<1, 1, 0, s>>>(dg, dev_view(g, (unsigned long long*)hist));
   MT_CUDA_TRY(cudaGetLastError());
   MT_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)C * 8, s));
-  if (g->n >= K) MT_TRY(count_enqueue(p, scratch, dg, table_device(t), 0, g->n, s));
+  if (g->n >= K) MT_TRY(count_enqueue(p, scratch, dg, table_view(t), 0, g->n, s));
   return MT_OK;
 }
 

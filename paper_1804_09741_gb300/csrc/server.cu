@@ -299,7 +299,8 @@ static mt_status step(mt_server* s, int32_t* completed) {
       tun.stack_cap = 0;
       tun.method = s->method;
       MT_TRY(count_configure_tuned(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C,
-                                   s->method == MT_METHOD_ENUMERATE ? nullptr : &tun));
+                                   s->method == MT_METHOD_ENUMERATE ? nullptr : &tun,
+                                   table_compact(t)));
       MT_TRY(ensure_capacity(s, ki, p.ws_bytes, chunks.size()));
       DevGraph* hg = R.h_graphs + off;
       for (size_t i = 0; i < chunks.size(); ++i) {
@@ -319,7 +320,7 @@ static mt_status step(mt_server* s, int32_t* completed) {
     for (int ki = 0; ki < 4; ++ki) {
       if (by_k[ki].empty()) continue;
       MT_CUDA_TRY(cudaStreamWaitEvent(s->kstream[ki], s->fork_ev, 0));
-      MT_TRY(count_enqueue(plans[ki], s->ws[ki], s->d_graphs[ki], table_device(s->tables[ki]), 0,
+      MT_TRY(count_enqueue(plans[ki], s->ws[ki], s->d_graphs[ki], table_view(s->tables[ki]), 0,
                            nmaxs[ki], s->kstream[ki]));
       MT_CUDA_TRY(cudaEventRecord(s->kdone_ev[ki], s->kstream[ki]));
       MT_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->kdone_ev[ki], 0));

@@ -27,6 +27,11 @@ struct mt_table {
   uint64_t nkeys = 0;
   uint32_t* table = nullptr;        // device, nkeys
   uint32_t* class_masks = nullptr;  // device, classes
+  // compact k = 6 form (see build_compact6): `table` holds the slots of
+  // (prefix class, relabelled words) instead of one slot per key
+  bool compact = false;
+  uint16_t* xclass = nullptr;       // device, 4096: prefix key -> class of the first 4 vertices
+  uint8_t* xmap = nullptr;          // device, 4096 x 256: prefix key -> word relabelling
 };
 
 namespace mt {
@@ -299,6 +304,169 @@ static mt_status build_table(int k, cudaStream_t s, mt_table** out) {
   return MT_OK;
 }
 
+// ---------------------------------------------------------- compact k = 6 form
+//
+// The k = 6 table has 2^30 slots (4 GiB), but a key is three parts: the first
+// four vertices X (positions 0..3, 12 key bits), the fifth vertex's word y (8
+// bits) and the sixth's z (10 bits).  Relabelling X into a canonical order of
+// its own (one of the 199 weakly connected 4-vertex classes; X is connected in
+// every enumerated set) and the words with it leaves the class of the whole
+// unchanged, so a table indexed by (class of X, relabelled y, relabelled z)
+// holds every class: 199 x 2^18 slots (208 MB).  Per prefix key it needs the
+// class of X and the relabelling of an 8-bit word (4 two-bit fields, one per
+// vertex of X); the sixth vertex's field for the fifth vertex is not moved.
+
+constexpr int kXKeys = 1 << 12;          // prefix keys (positions 1..3 of a 6-vertex key)
+constexpr int kXClasses = 199;           // weakly connected 4-vertex classes
+constexpr int kXLow = 18;                // bits of y and z in a 6-vertex key
+
+// The 4-vertex prefix of a 6-vertex key, as an 8x8 bit matrix.
+__device__ __forceinline__ uint64_t xkey_matrix(uint32_t xk) { return key_to_matrix(xk << kXLow, 6); }
+
+// For every prefix key: the smallest 4-vertex canonical-layout mask over the 24
+// orderings sigma (new position i holds old vertex sigma(i)), the ordering that
+// reaches it, and whether X is weakly connected.  Marks the connected minima.
+__global__ void k_xprefix(uint16_t* xcanon, uint8_t* xsigma, uint32_t* xbits, int32_t* xrep) {
+  const int xk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xk >= kXKeys) return;
+  const uint64_t x0 = xkey_matrix((uint32_t)xk);
+  uint32_t best = 0xFFFFFFFFu, best_sigma = 0;
+  for (int c = 0; c < 24; ++c) {
+    // the c-th ordering of 4 vertices (factorial number system)
+    int avail[4] = {0, 1, 2, 3}, sig[4];
+    int r = c;
+    for (int i = 0, f = 6; i < 4; ++i) {
+      const int d = r / f;
+      r %= f;
+      sig[i] = avail[d];
+      for (int j = d; j < 3 - i; ++j) avail[j] = avail[j + 1];
+      f = i < 3 ? f / (3 - i) : 1;
+    }
+    uint64_t y = 0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        if ((x0 >> (8 * sig[i] + sig[j])) & 1ull) y |= 1ull << (8 * i + j);
+    const uint32_t mask = matrix_to_mask(y, 4);
+    if (mask < best) {
+      best = mask;
+      best_sigma = (uint32_t)(sig[0] | (sig[1] << 2) | (sig[2] << 4) | (sig[3] << 6));
+    }
+  }
+  xcanon[xk] = (uint16_t)best;
+  xsigma[xk] = (uint8_t)best_sigma;
+  const bool conn = matrix_connected(x0, 4);
+  if (conn) atomicOr(&xbits[best >> 5], 1u << (best & 31u));
+  // the prefix key whose own matrix is the canonical one represents the class
+  if (conn && matrix_to_mask(x0, 4) == best) xrep[best] = xk;
+}
+
+// Class of each prefix key (rank of its canonical mask among the connected
+// ones; 0xFFFF if X is disconnected) and the relabelling of all 256 words.
+__global__ void k_xtables(const uint16_t* xcanon, const uint8_t* xsigma, const uint32_t* xbits,
+                          uint16_t* xclass, uint8_t* xmap) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kXKeys * 256) return;
+  const int xk = t >> 8, w = t & 255;
+  const uint32_t sg = xsigma[xk];
+  uint32_t out = 0;
+  for (int i = 0; i < 4; ++i) out |= ((w >> (2 * ((sg >> (2 * i)) & 3u))) & 3u) << (2 * i);
+  xmap[t] = (uint8_t)out;
+  if (w == 0) {
+    const uint32_t c = xcanon[xk];
+    const bool conn = matrix_connected(xkey_matrix((uint32_t)xk), 4);
+    uint32_t rank = 0;
+    for (uint32_t q = 0; q < (c >> 5); ++q) rank += __popc(xbits[q]);
+    rank += __popc(xbits[c >> 5] & ((1u << (c & 31u)) - 1u));
+    xclass[xk] = conn ? (uint16_t)rank : (uint16_t)0xFFFFu;
+  }
+}
+
+// Representative prefix key of each class, in class order.
+__global__ void k_xreps(const uint32_t* xbits, const int32_t* xrep, int32_t* reps) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int r = 0;
+  for (uint32_t c = 0; c < kXKeys && r < kXClasses; ++c)
+    if ((xbits[c >> 5] >> (c & 31u)) & 1u) reps[r++] = xrep[c];
+}
+
+// compact[c << 18 | low] = full[rep(c) << 18 | low]
+__global__ void k_xgather(const uint32_t* full, const int32_t* reps, uint32_t* compact) {
+  const uint64_t n = (uint64_t)kXClasses << kXLow;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = (uint32_t)(i >> kXLow), low = (uint32_t)(i & ((1u << kXLow) - 1u));
+    compact[i] = full[((uint64_t)reps[c] << kXLow) | low];
+  }
+}
+
+static mt_status build_compact6(cudaStream_t s, mt_table** out) {
+  mt_table* full = nullptr;
+  MT_TRY(build_table(6, s, &full));
+  mt_table* t = new mt_table();
+  t->k = 6;
+  t->classes = full->classes;
+  t->class_masks = full->class_masks;
+  full->class_masks = nullptr;
+  t->compact = true;
+  t->nkeys = (uint64_t)kXClasses << kXLow;
+  uint16_t* xcanon = nullptr;
+  uint8_t* xsigma = nullptr;
+  uint32_t* xbits = nullptr;
+  int32_t *xrep = nullptr, *reps = nullptr;
+  cudaError_t e = cudaMalloc(&t->table, t->nkeys * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&t->xclass, kXKeys * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&t->xmap, kXKeys * 256);
+  if (e == cudaSuccess) e = cudaMallocAsync(&xcanon, kXKeys * 2, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&xsigma, kXKeys, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&xbits, kXKeys / 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&xrep, kXKeys * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&reps, kXClasses * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(xbits, 0, kXKeys / 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(reps, 0, kXClasses * 4, s);
+  int32_t nreps = 0;
+  if (e == cudaSuccess) {
+    k_xprefix<<<kXKeys / 256, 256, 0, s>>>(xcanon, xsigma, xbits, xrep);
+    k_xtables<<<kXKeys, 256, 0, s>>>(xcanon, xsigma, xbits, t->xclass, t->xmap);
+    k_xreps<<<1, 32, 0, s>>>(xbits, xrep, reps);
+    k_xgather<<<1024, 256, 0, s>>>(full->table, reps, t->table);
+    e = cudaGetLastError();
+  }
+  // the number of connected 4-vertex classes must be 199
+  std::vector<uint32_t> hb(kXKeys / 32);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hb.data(), xbits, kXKeys / 8, cudaMemcpyDeviceToHost, s);
+  if (xcanon) cudaFreeAsync(xcanon, s);
+  if (xsigma) cudaFreeAsync(xsigma, s);
+  if (xbits) cudaFreeAsync(xbits, s);
+  if (xrep) cudaFreeAsync(xrep, s);
+  if (reps) cudaFreeAsync(reps, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (uint32_t w : hb) nreps += __builtin_popcount(w);
+  cudaFree(full->table);
+  delete full;
+  if (e != cudaSuccess || nreps != kXClasses) {
+    if (e != cudaSuccess) set_last_error(cudaGetErrorString(e));
+    else set_last_error("compact table: " + std::to_string(nreps) + " prefix classes");
+    cudaFree(t->table);
+    cudaFree(t->class_masks);
+    cudaFree(t->xclass);
+    cudaFree(t->xmap);
+    delete t;
+    return e == cudaErrorMemoryAllocation ? MT_ENOMEM : MT_ECUDA;
+  }
+  *out = t;
+  return MT_OK;
+}
+
+TableView table_view(const mt_table* t) {
+  TableView v;
+  v.slots = t->table;
+  v.xclass = t->compact ? t->xclass : nullptr;
+  v.xmap = t->compact ? t->xmap : nullptr;
+  return v;
+}
+bool table_compact(const mt_table* t) { return t->compact; }
+
 const uint32_t* table_device(const mt_table* t) { return t->table; }
 int table_k(const mt_table* t) { return t->k; }
 uint32_t table_classes(const mt_table* t) { return t->classes; }
@@ -315,11 +483,25 @@ mt_status mt_table_build(int k, void* stream, mt_table** out) {
   return build_table(k, (cudaStream_t)stream, out);
 }
 
+mt_status mt_table_build_compact(int k, void* stream, mt_table** out) {
+  if (!out) return MT_EINVAL;
+  if (k != 6) return MT_EUNSUPPORTED;
+  return build_compact6((cudaStream_t)stream, out);
+}
+
+mt_status mt_table_is_compact(const mt_table* t, int* compact) {
+  if (!t || !compact) return MT_EINVAL;
+  *compact = t->compact ? 1 : 0;
+  return MT_OK;
+}
+
 mt_status mt_table_free(mt_table* t) {
   if (!t) return MT_OK;
   cudaDeviceSynchronize();
   cudaFree(t->table);
   cudaFree(t->class_masks);
+  if (t->xclass) cudaFree(t->xclass);
+  if (t->xmap) cudaFree(t->xmap);
   delete t;
   return MT_OK;
 }
