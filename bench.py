@@ -138,12 +138,37 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed (string
+    and character literals kept), so that a comment-only edit keeps the hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in ("count.cu", "count.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1804_09741_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1804_09741_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

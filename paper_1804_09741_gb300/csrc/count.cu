@@ -9,32 +9,39 @@
 // every remaining candidate completes one k-set.
 //
 // GPU mapping (one warp = one depth-first walk, lanes cooperate):
-//  * per warp a "relation word" lab[u] for every vertex (8 bits for k <= 5, 16
-//    for k = 6): bits 2p, 2p+1 hold the A/B/C relation (Sec. 2) of u to the
-//    vertex at position p of the current set.  Pushing w at position p scans
-//    delta(w) above the root coalesced (the row-scan strategy of Sec. 3.1),
-//    ORs its relation bits into lab[u] and, with one ballot, appends to the
-//    candidate stack every u whose word was zero (exclusive neighbour).
-//    Popping clears the same bits;
+//  * per warp a "relation word" lab[u] for every vertex: bits 2p, 2p+1 hold the
+//    A/B/C relation (Sec. 2) of u to the vertex at position p of the current
+//    set.  Pushing w at position p scans delta(w) above the root coalesced
+//    (the row-scan strategy of Sec. 3.1), ORs its relation bits into lab[u]
+//    and, with one ballot, appends to the candidate stack every u with no
+//    relation to the earlier positions (exclusive neighbour).  Popping clears
+//    the same bits.  Words are 8, 16 or 32 bits (see LabT): the bits above the
+//    first k-2 positions are slots for the (k-1)-th choices;
 //  * candidate lists of all levels live in one per-warp stack: level p+1's list
 //    is the unused tail of level p's list followed by the newly appended
 //    exclusive neighbours, so no list is ever copied;
-//  * level state (cursor, ends, pushed vertex, key prefix) lives in registers of
-//    lane p and is read with shuffles;
-//  * choosing the (k-1)-th vertex y finishes its k-sets in place: y's row scan
-//    classifies the exclusive neighbours (their word is the arc code to y), and
-//    each remaining candidate's key is the key prefix OR its word shifted to the
-//    last position -- no per-subgraph adjacency test; equal keys of a batch of
-//    32 leaves share one table read (match_any);
+//  * the current level's state (cursor, ends, key prefix) lives in warp-uniform
+//    registers; suspended levels wait in a small per-warp stack in shared
+//    memory;
+//  * choosing the (k-1)-th vertex finishes its k-sets in place, for up to GS
+//    choices at once: the choices' rows, concatenated over the lanes, mark
+//    each choice's slot in its neighbours' words and classify the exclusive
+//    neighbours (their word is the arc code to the choice); then one pass over
+//    the remaining candidates classifies every choice's leaves from the words
+//    (key prefix OR word) and clears the slots again -- no per-subgraph
+//    adjacency test; equal keys of a pass share one table read (match_any);
 //  * MT_METHOD_CELLS stops one level earlier and counts the last two vertices
 //    per pair of cells (Algorithm 1 of Sec. 3; see pair_level below);
-//  * histograms: per-block shared-memory counters for k <= 5 (13 / 199 / 9,364
-//    classes), 64-bit global atomics for k = 6.
+//  * histograms: per-block shared-memory 32-bit counters for k <= 5 (13 / 199
+//    / 9,364 classes), the graph's 64-bit global counters for k = 6, both
+//    updated with reductions that return nothing (PTX red).
 //
 // Work items are (graph, root, first-level branch range) or, for expensive
 // branches, (graph, root, branch, second-level choice range); a planner sizes
 // them from per-branch cost estimates.  Blocks work graph by graph, warps take
-// the items of the block's current graph from that graph's queue.
+// the items of the block's current graph from that graph's queue, and a warp
+// that runs out takes halves of its block-mates' remaining ranges (work
+// donation).
 #include <algorithm>
 #include <type_traits>
 
