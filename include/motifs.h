@@ -247,6 +247,23 @@ mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
  *   (mt_last_error() gives both sizes; use mt_count), MT_ECUDA. */
 mt_status mt_count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* hist, void* stream);
 
+/* Caller-provided scratch for the counts of one graph handle (the paper has no
+ * counterpart; for callers whose device memory comes from their own allocator,
+ * e.g. a torch tensor).  mt_workspace_query: the bytes of scratch that
+ * mt_count / mt_count_roots of `g` at k need (automatic launch; a tuned launch
+ * may need more).  Errors: MT_EINVAL, MT_EUNSUPPORTED (k outside 3..6).
+ * mt_set_workspace: attach `bytes` of DEVICE memory at `ws` (256-byte aligned;
+ * the caller keeps ownership and must keep it alive until it is detached or
+ * the graph is freed) as the scratch of every later count of `g`; those counts
+ * then allocate no device memory, and one that needs more than `bytes` fails
+ * with MT_EINVAL (mt_last_error gives both sizes).  ws = NULL detaches it (the
+ * library allocates its own scratch again).  Synchronises the device (an
+ * earlier count may still use the previous scratch); frees scratch the library
+ * had allocated for `g`.  Counts on one handle share its scratch: order them on
+ * one stream.  Errors: MT_EINVAL (not device memory, misaligned, empty). */
+mt_status mt_workspace_query(const mt_graph* g, int k, size_t* bytes);
+mt_status mt_set_workspace(mt_graph* g, void* ws, size_t bytes);
+
 /* Diagnostics of the last counting call on this graph: number of work items
  * the planner made, the device error word (0 = fine; non-zero = stack or queue
  * overflow, the histogram is invalid) and the enumerator's time in ms (device

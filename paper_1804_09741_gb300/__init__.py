@@ -64,6 +64,8 @@ SIGNATURES = {
     "mt_count_tuned": (ctypes.c_int, [_vp, _vp, _vp, _P(Tuning), _vp]),
     "mt_count_stats": (ctypes.c_int, [_vp, _P(_u64), _P(_u32), _P(ctypes.c_float)]),
     "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mt_workspace_query": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_size_t)]),
+    "mt_set_workspace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "mt_randomize": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_randomize_dyads": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_batch_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(_vp)]),
@@ -299,6 +301,25 @@ def count_noalloc(g: Graph, t: Table, out=None, stream=None):
     _check(_lib.mt_count_noalloc(g.handle, t.handle, out.data_ptr(), _stream(stream)),
            "mt_count_noalloc")
     return out
+
+
+def workspace_query(g: Graph, k: int) -> int:
+    """Bytes of scratch a count of `g` at k needs (mt_workspace_query)."""
+    out = ctypes.c_size_t()
+    _check(_lib.mt_workspace_query(g.handle, int(k), ctypes.byref(out)), "mt_workspace_query")
+    return int(out.value)
+
+
+def set_workspace(g: Graph, buf=None):
+    """Attach a device buffer (a CUDA tensor; it is kept alive with the handle)
+    as the scratch of the counts of `g` (mt_set_workspace); None detaches."""
+    if buf is None:
+        _check(_lib.mt_set_workspace(g.handle, None, 0), "mt_set_workspace")
+        g._workspace = None
+        return
+    nbytes = buf.numel() * buf.element_size()
+    _check(_lib.mt_set_workspace(g.handle, buf.data_ptr(), nbytes), "mt_set_workspace")
+    g._workspace = buf
 
 
 def count_stats(g: Graph):

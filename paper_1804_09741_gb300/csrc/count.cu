@@ -1246,6 +1246,11 @@ mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
   return MT_OK;
 }
 
+// Scratch of a one-graph count: plan workspace + the DevGraph + a histogram.
+static size_t count_scratch_bytes(const CountPlan& p, uint32_t C) {
+  return p.ws_bytes + 256 + round16((size_t)C * 8);
+}
+
 // Plain one-graph count with the workspace cached in the graph handle.
 static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist,
                            int32_t rb, int32_t re, const mt_tuning* tuning, cudaStream_t s) {
@@ -1256,8 +1261,12 @@ static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist
   MT_TRY(count_configure_tuned(&p, K, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1), C,
                                tuning, table_compact(t)));
   // workspace: plan scratch + the DevGraph + a device histogram
-  const size_t extra = 256 + round16((size_t)C * 8);
-  const size_t need = p.ws_bytes + extra;
+  const size_t need = count_scratch_bytes(p, C);
+  if (!g->ws_owned && g->ws_bytes < need) {
+    set_last_error("attached workspace holds " + std::to_string(g->ws_bytes) +
+                   " bytes, this count needs " + std::to_string(need));
+    return MT_EINVAL;
+  }
   if (g->ws_bytes < need) {
     if (g->ws) {
       // an earlier count may still use the old scratch, on any stream
@@ -1335,6 +1344,38 @@ mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
                  tuning->method < 0 || tuning->method > 1))
     return MT_EINVAL;
   return count_one(g, t, hist, 0, g->n, tuning, (cudaStream_t)stream);
+}
+
+mt_status mt_workspace_query(const mt_graph* g, int k, size_t* bytes) {
+  if (!g || !bytes) return MT_EINVAL;
+  if (k < 3 || k > 6) return MT_EUNSUPPORTED;
+  CountPlan p;
+  MT_TRY(count_configure_tuned(&p, k, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1),
+                               kNumClasses[k], nullptr));
+  *bytes = count_scratch_bytes(p, kNumClasses[k]);
+  return MT_OK;
+}
+
+mt_status mt_set_workspace(mt_graph* g, void* ws, size_t bytes) {
+  if (!g) return MT_EINVAL;
+  if (ws) {
+    cudaPointerAttributes attr;
+    const bool dev = cudaPointerGetAttributes(&attr, ws) == cudaSuccess &&
+                     attr.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (!dev || ((uintptr_t)ws & 255u) || bytes == 0) {
+      set_last_error("mt_set_workspace: ws must be device memory, 256-byte aligned, non-empty");
+      return MT_EINVAL;
+    }
+  }
+  // an earlier count may still use the current scratch, on any stream
+  MT_CUDA_TRY(cudaDeviceSynchronize());
+  if (g->ws && g->ws_owned) cudaFree(g->ws);
+  g->ws = ws;
+  g->ws_bytes = ws ? bytes : 0;
+  g->ws_owned = ws == nullptr;
+  g->stats_valid = false;
+  return MT_OK;
 }
 
 mt_status mt_count_stats(const mt_graph* g, uint64_t* items, uint32_t* err, float* ms) {

@@ -325,7 +325,7 @@ mt_status mt_graph_free(mt_graph* g) {
   if (!g) return MT_OK;
   cudaDeviceSynchronize();
   if (g->mem) cudaFree(g->mem);
-  if (g->ws) cudaFree(g->ws);
+  if (g->ws && g->ws_owned) cudaFree(g->ws);
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
   delete g;

@@ -16,9 +16,11 @@ struct mt_graph {
   void* mem = nullptr;         // one allocation backing all of the above
   bool pooled = false;         // mem came from the stream-ordered pool (cudaMallocAsync)
 
-  // Counting scratch, grown on demand by mt_count.
+  // Counting scratch, grown on demand by mt_count, or the caller's buffer
+  // attached by mt_set_workspace (ws_owned false: never grown or freed here).
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  bool ws_owned = true;
   // Where the last count left its error word and item count inside `ws`.
   bool stats_valid = false;
   size_t off_err = 0, off_nitems = 0;
