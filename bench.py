@@ -285,17 +285,21 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    all_subgraphs = subgraphs_per_step  # per step, all ranks (their null graphs differ)
     if dist:
         tt = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
+        ts = torch.tensor([subgraphs_per_step], dtype=torch.int64, device="cuda")
+        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+        all_subgraphs = int(ts.item())
         dist.barrier()
-    value = subgraphs_per_step * args.steps * world / (total_ms / 1000.0)
+    value = all_subgraphs * args.steps / (total_ms / 1000.0)
 
     # end to end through the public API with host buffers: load the graph from
     # host CSR, run the one-shot batch into host histograms and z-scores.
     e2e = None
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e:  # every rank its own batch; the slowest rank's time counts
         # inputs in pinned host memory, as a caller streaming graphs would keep them
         rp_t = torch.empty(g.n + 1, dtype=torch.int32, pin_memory=True)
         col_t = torch.empty(max(g.m, 1), dtype=torch.int32, pin_memory=True)
@@ -303,6 +307,8 @@ def run_ours(args, world, rank, local):
         col_t.numpy()[:g.m] = g.col
         rp, col = rp_t.numpy(), col_t.numpy()[:g.m]
         e2e_times = []
+        if dist:
+            dist.barrier()
         for _ in range(2):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -315,11 +321,16 @@ def run_ours(args, world, rank, local):
             e2e_times.append(time.perf_counter() - t1)
             gg.free()
         assert int(hh.sum()) == subgraphs_per_step
-        h2d = rp.nbytes + col.nbytes + (seeds.nbytes if R else 0)
-        d2h = (R + 1) * C * 8 + (C * 8 if R else 0)
-        e2e = {"value": subgraphs_per_step / min(e2e_times), "unit": "subgraphs/s",
+        h2d = world * (rp.nbytes + col.nbytes + (seeds.nbytes if R else 0))
+        d2h = world * ((R + 1) * C * 8 + (C * 8 if R else 0))
+        e2e_s = min(e2e_times)
+        if dist:
+            te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e_s = float(te.item())
+        e2e = {"value": all_subgraphs / e2e_s, "unit": "subgraphs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1000 * min(e2e_times)}
+               "ms_per_step": 1000 * e2e_s}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
