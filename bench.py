@@ -350,13 +350,13 @@ def run_ours(args, world, rank, local):
     roofline = None
     if R and count_ms:
         cm = statistics.mean(count_ms)
-        ops = OPS_PER_SUBGRAPH * subgraphs_per_step
+        ops = ops_per_subgraph(k) * subgraphs_per_step
         achieved = ops / (cm / 1000.0) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                     "frac": achieved / alu_peak,
                     "traffic": _captured_traffic(args.method, args.workload, R),
                     "kernel": "k_count (enumerate+classify+count)", "kernel_ms": cm,
-                    "ops_per_subgraph": OPS_PER_SUBGRAPH,
+                    "ops_per_subgraph": ops_per_subgraph(k),
                     "peak_source": f"152 SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_mhz} MHz "
                                    f"({src} sm_max_mhz)"}
 
@@ -625,10 +625,12 @@ def measure_serving(mt, torch, have_tables, num=32, seed=0, method=0, round_cost
             "all_ok": ok, "method": "cells" if method else "enumerate"}
 
 
-# Algorithmic integer operations per classified subgraph in the leaf loop:
-# candidate read, relation-word read, shift + or into the key, table read,
-# histogram add.
-OPS_PER_SUBGRAPH = 6
+def ops_per_subgraph(k: int) -> int:
+    """Algorithmic integer operations per classified k-subgraph: one table
+    read, one histogram increment and the 2(k-1) direction-bit tests that fix
+    the last vertex's arcs to the others (the enumeration's bookkeeping is not
+    counted)."""
+    return 2 + 2 * (k - 1)
 
 
 def main():
