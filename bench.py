@@ -195,6 +195,8 @@ def _config(args, w, world):
          "null_graphs": nulls, "swaps_per_null": 10 * w["m"] if nulls else 0,
          "graphs_per_step": 1 + nulls, "parallelism": f"replicas{world}",
          "l2": "flushed between timed steps (256 MiB write)", "method": args.method}
+    if getattr(args, "compact_table", False):
+        c["table"] = "compact (199 x 2^18 slots)"
     return c
 
 
@@ -220,7 +222,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    table = mt.table_build(k)
+    table = mt.table_build(k, compact=args.compact_table)
     table_ms = 1000 * (time.perf_counter() - t0)
     dg = mt.graph_from(g)
     C = table.num_classes
@@ -648,6 +650,8 @@ def main():
                     help="counting method of the main measurement (recorded in config)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the k=6 batch, plain-vs-batched and serving measurements")
+    ap.add_argument("--compact-table", action="store_true",
+                    help="k=6 only: count with the compact table (recorded in config)")
     ap.add_argument("--nulls", type=int, default=None,
                     help="number of null graphs (default: the workload's); smaller values make "
                          "the small cases profiled under ncu, recorded in config")
