@@ -28,9 +28,9 @@ sys.path.insert(0, ROOT)
 import synthetic as syn  # noqa: E402
 
 # Root sample the CPU oracle times (k-sets whose smallest vertex is in it):
-# about 10-15 s of oracle work on 16 host cores for the two null-model
-# workloads (7.7e7 and 7.0e6 k-sets), the whole graph for the small ones.
-CPU_SAMPLE = {"nullmodel_k5": (60, 200), "nullmodel_k6": (100, 200), "chunglu_k4": (0, 2000),
+# about 7-12 s of oracle work on 16 host cores for the two null-model
+# workloads (1.3e8 and 2.1e7 k-sets), the whole graph for the small ones.
+CPU_SAMPLE = {"nullmodel_k5": (30, 200), "nullmodel_k6": (60, 200), "chunglu_k4": (0, 2000),
               "uniform_k3": (0, 300)}
 INT32_LANES_PER_SM = 128
 
