@@ -137,6 +137,20 @@ static void release_request(mt_server* s, SrvRequest* r) {
   if (r->state == 1 || r->state == 2) s->used -= std::min(s->used, r->bytes);
 }
 
+// A request that cannot run (its launch cannot be configured): it fails alone
+// with `st`, its memory and slot are released.
+static void fail_request(mt_server* s, RoundBuf& R, SrvRequest* r, mt_status st) {
+  release_request(s, r);
+  if (r->h_result) s->pinned_free[r->k - 3].push_back(r->h_result);
+  r->h_result = nullptr;
+  r->state = 3;
+  r->status = st;
+  r->t_done = now_ms(s);
+  s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+  auto f = std::find(R.finishing.begin(), R.finishing.end(), r);
+  if (f != R.finishing.end()) R.finishing.erase(f);
+}
+
 static void admit(mt_server* s) {
   bool loaded = false;
   while (!s->pending.empty() && (int)s->active.size() < s->max_slots) {
@@ -298,9 +312,17 @@ static mt_status step(mt_server* s, int32_t* completed) {
       tun.warps_per_block = 0;
       tun.stack_cap = 0;
       tun.method = s->method;
-      MT_TRY(count_configure_tuned(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C,
-                                   s->method == MT_METHOD_ENUMERATE ? nullptr : &tun,
-                                   table_compact(t)));
+      const mt_status cst =
+          count_configure_tuned(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C,
+                                s->method == MT_METHOD_ENUMERATE ? nullptr : &tun, table_compact(t));
+      if (cst != MT_OK) {
+        // this k cannot run with its table and the server's method (e.g. the
+        // cell method on a compact k = 6 table): its requests fail alone,
+        // before any of their roots is marked as counted
+        for (auto& c : chunks) fail_request(s, R, c.r, cst);
+        chunks.clear();
+        continue;
+      }
       MT_TRY(ensure_capacity(s, ki, p.ws_bytes, chunks.size()));
       DevGraph* hg = R.h_graphs + off;
       for (size_t i = 0; i < chunks.size(); ++i) {

@@ -124,3 +124,25 @@ def test_bad_request_fails_alone(tables):
     with pytest.raises(mt.MotifsError):
         srv.submit(4, syn.Graph(2, np.array([0, 1, 1], np.int32), np.array([0], np.int32)))
     srv.free()
+
+
+def test_unsupported_table_method_pair_fails_alone(tables):
+    """The cell method cannot use a compact k = 6 table: the server fails those
+    requests alone (status MT_EUNSUPPORTED, no partial result) and serves the
+    others in the same rounds."""
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server, run_stream
+    compact6 = mt.table_build(6, compact=True)
+    srv = Server({5: tables[5], 6: compact6}, memory_budget=2 << 30, max_slots=8,
+                 round_cost=2e6, method=mt.METHOD_CELLS)
+    g5 = syn.chung_lu_digraph(400, 1200, 2.3, 30, 0.2, 7)
+    g6 = syn.chung_lu_digraph(120, 360, 2.3, 20, 0.2, 8)
+    reqs = [(6, g6), (5, g5), (6, g6)]
+    out, lat, wall = run_stream(srv, reqs)
+    assert out[0][0] == 3 and out[0][2] == mt.MT_EUNSUPPORTED and out[0][1] is None
+    assert out[2][0] == 3 and out[2][2] == mt.MT_EUNSUPPORTED
+    assert out[1][0] == 2
+    np.testing.assert_array_equal(out[1][1], alone(mt, tables[5], g5))
+    assert srv.used_bytes() == 0
+    srv.free()
+    compact6.free()
