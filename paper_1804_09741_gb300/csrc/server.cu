@@ -312,18 +312,20 @@ static mt_status step(mt_server* s, int32_t* completed) {
       tun.warps_per_block = 0;
       tun.stack_cap = 0;
       tun.method = s->method;
-      const mt_status cst =
+      mt_status cst =
           count_configure_tuned(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C,
                                 s->method == MT_METHOD_ENUMERATE ? nullptr : &tun, table_compact(t));
+      if (cst == MT_OK) cst = ensure_capacity(s, ki, p.ws_bytes, chunks.size());
       if (cst != MT_OK) {
-        // this k cannot run with its table and the server's method (e.g. the
-        // cell method on a compact k = 6 table): its requests fail alone,
-        // before any of their roots is marked as counted
+        // this k cannot run (its table and the server's method do not go
+        // together, e.g. the cell method on a compact k = 6 table, or its
+        // scratch cannot be allocated): its requests fail alone, before any
+        // of their roots is marked as counted
         for (auto& c : chunks) fail_request(s, R, c.r, cst);
         chunks.clear();
+        cudaGetLastError();  // an allocation failure is not sticky: clear it
         continue;
       }
-      MT_TRY(ensure_capacity(s, ki, p.ws_bytes, chunks.size()));
       DevGraph* hg = R.h_graphs + off;
       for (size_t i = 0; i < chunks.size(); ++i) {
         hg[i] = dev_view(chunks[i].r->g, chunks[i].r->d_hist);
