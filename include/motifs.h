@@ -394,7 +394,10 @@ mt_status mt_server_step(mt_server* s, int32_t* completed, int32_t* active, int3
 /* State of a request: 0 pending, 1 active, 2 done, 3 failed.  When done and
  * `hist` (HOST uint64[C]) is given, copies H_k and forgets the request.  A
  * failed request returns its error (MT_EINVAL for a duplicate arc found on the
- * device, MT_EBUSY when it can never fit the budget) and is forgotten.
+ * device, MT_EBUSY when it can never fit the budget, MT_EUNSUPPORTED when its
+ * k's table and the server's method do not go together -- the cell method
+ * with a compact k = 6 table --, MT_ENOMEM when a round's scratch for its k
+ * cannot be allocated) and is forgotten; other requests are not affected.
  * `latency_ms` = completion time - submission time on the host clock. */
 mt_status mt_server_result(mt_server* s, uint64_t id, int32_t* state, uint64_t* hist,
                            double* latency_ms);
