@@ -146,3 +146,21 @@ def test_unsupported_table_method_pair_fails_alone(tables):
     assert srv.used_bytes() == 0
     srv.free()
     compact6.free()
+
+
+def test_compact_k6_table_in_the_server(tables):
+    """The per-subgraph method serves k = 6 requests from the compact table;
+    results equal the full table's one-graph counts."""
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server, poisson_arrivals, run_stream
+    compact6 = mt.table_build(6, compact=True)
+    srv = Server({5: tables[5], 6: compact6}, memory_budget=2 << 30, max_slots=8,
+                 round_cost=2e6)
+    reqs = [(6, syn.chung_lu_digraph(n, 3 * n, 2.3, 20, 0.2, 40 + n)) for n in (60, 150, 240)]
+    reqs.append((5, syn.chung_lu_digraph(300, 900, 2.3, 30, 0.2, 9)))
+    out, lat, wall = run_stream(srv, reqs, poisson_arrivals(len(reqs), 300.0, 2))
+    for (k, g), (st, hist, status) in zip(reqs, out):
+        assert st == 2, status
+        np.testing.assert_array_equal(hist, alone(mt, tables[k], g))
+    srv.free()
+    compact6.free()
