@@ -1,4 +1,4 @@
-"""Python driver of the continuous-batching request server (mt_server_* in
+"""Python front end of the continuous-batching request server (mt_server_* in
 include/motifs.h): submission, the round loop, Poisson arrivals and latency
 percentiles.  All counting runs in the library's kernels."""
 from __future__ import annotations
