@@ -97,3 +97,23 @@ def test_null_handles_rejected(mtlib):
     assert mtlib.mt_table_build(2, None, ctypes.byref(ctypes.c_void_p())) == 2
     assert mtlib.mt_randomize(None, 1, 1, None, ctypes.byref(ctypes.c_void_p())) == 1
     assert mtlib.mt_batch_create(None, None, 1, 1, ctypes.byref(ctypes.c_void_p())) == 1
+
+
+def test_header_compiles_as_plain_c_and_links(mtlib, tmp_path):
+    """include/motifs.h is a C header: a C99 program using it compiles with
+    warnings as errors, links against the library and runs its host-only calls
+    (no GPU)."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    import subprocess
+    from paper_1804_09741_gb300 import build as b
+    libdir = b.BUILD
+    exe = str(tmp_path / "host_calls")
+    subprocess.check_call([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_abi", "host_calls.c"),
+                           "-L", libdir, "-lmotifs", "-Wl,-rpath," + libdir, "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert "c abi host calls ok" in out.stdout
