@@ -262,6 +262,16 @@ mt_status mt_count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* hist,
  * had allocated for `g`.  Counts on one handle share its scratch: order them on
  * one stream.  Errors: MT_EINVAL (not device memory, misaligned, empty). */
 mt_status mt_workspace_query(const mt_graph* g, int k, size_t* bytes);
+
+/* Limit, in nanoseconds, of the device wait of a warp that has run out of work
+ * and waits for work handed over by the other warps of its block (the wait is
+ * also bounded by a poll count).  When it expires the warp stops and the count
+ * reports MT_ETIMEOUT (its histogram is then incomplete).  Applies to the
+ * launches enqueued after the call, process-wide; 0 restores the default of
+ * 60 s.  A fault-injection hook: a limit of a few nanoseconds makes any count
+ * whose warps go idle at different times report MT_ETIMEOUT, without a GPU
+ * fault or hang.  The paper has no counterpart. */
+mt_status mt_set_wait_limit(uint64_t ns);
 mt_status mt_set_workspace(mt_graph* g, void* ws, size_t bytes);
 
 /* Diagnostics of the last counting call on this graph: number of work items

@@ -66,6 +66,7 @@ SIGNATURES = {
     "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_workspace_query": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_size_t)]),
     "mt_set_workspace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "mt_set_wait_limit": (ctypes.c_int, [_u64]),
     "mt_randomize": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_randomize_dyads": (ctypes.c_int, [_vp, _u64, _u64, _vp, _P(_vp)]),
     "mt_batch_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u64, _P(_vp)]),
@@ -320,6 +321,12 @@ def set_workspace(g: Graph, buf=None):
     nbytes = buf.numel() * buf.element_size()
     _check(_lib.mt_set_workspace(g.handle, buf.data_ptr(), nbytes), "mt_set_workspace")
     g._workspace = buf
+
+
+def set_wait_limit(ns: int = 0):
+    """mt_set_wait_limit: the idle-wait limit of later launches (0 = default)."""
+    load_library()
+    _check(_lib.mt_set_wait_limit(int(ns)), "mt_set_wait_limit")
 
 
 def count_stats(g: Graph):

@@ -68,7 +68,10 @@ constexpr int kDonSlots = 32;
 // idle time (ns) after which a warp gives up and reports kErrWaitLimit.
 constexpr int kLockTries = 1 << 24;
 constexpr int kIdlePolls = 1 << 28;
-constexpr unsigned long long kIdleNs = 60ull * 1000 * 1000 * 1000;
+constexpr unsigned long long kIdleNs = 60ull * 1000 * 1000 * 1000;  // default; mt_set_wait_limit
+
+// Idle-wait limit (ns) given to the launches enqueued from now on.
+static unsigned long long g_idle_ns = kIdleNs;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -363,6 +366,7 @@ struct CountArgs {
   int G, nmax, nu_cap, cap;
   uint32_t classes;
   int graph_bytes, hist_bytes, lab_bytes, buf_bytes, cell_bytes, map_bytes;
+  unsigned long long idle_ns;  // a warp waiting for donated work gives up after this
 };
 
 // Cells of the last two positions (combinatorial counting): a relation word to
@@ -682,7 +686,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           block_unlock();
           if (r >= 0) return r;
         }
-        if (global_ns() - t0 > kIdleNs) break;
+        if (global_ns() - t0 > a.idle_ns) break;
         __nanosleep(256);
       }
       atomicOr(&a.hdr->err, kErrWaitLimit);
@@ -1212,6 +1216,7 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
   a.xclass = p.compact ? table.xclass : nullptr;
   a.xmap = p.compact ? table.xmap : nullptr;
   a.map_bytes = (int)p.map_bytes;
+  a.idle_ns = g_idle_ns;
   a.lab_global = lab;
   a.G = p.G;
   a.nmax = p.nmax;
@@ -1344,6 +1349,11 @@ mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
                  tuning->method < 0 || tuning->method > 1))
     return MT_EINVAL;
   return count_one(g, t, hist, 0, g->n, tuning, (cudaStream_t)stream);
+}
+
+mt_status mt_set_wait_limit(uint64_t ns) {
+  g_idle_ns = ns ? (unsigned long long)ns : kIdleNs;
+  return MT_OK;
 }
 
 mt_status mt_workspace_query(const mt_graph* g, int k, size_t* bytes) {

@@ -93,3 +93,22 @@ def test_probe_rates_are_measured():
     assert 1e9 < g < 1e14 and 1e8 < a < 1e14
     with pytest.raises(mt.MotifsError):
         mt.probe_rates(1000, 1 << 14)  # not a power of two
+
+
+def test_expired_idle_wait_reports_timeout(t5):
+    """Fault injection from the host: with an idle-wait limit of a few
+    nanoseconds, warps that run out of work before their block-mates give up
+    and the count reports MT_ETIMEOUT (no GPU fault, trap or hang); with the
+    limit restored the same count is exact again."""
+    import paper_1804_09741_gb300 as mt
+    g = syn.workload_graph("nullmodel_k5")
+    dg = mt.graph_from(g)
+    want = mt.count_host(dg, t5)
+    try:
+        mt.set_wait_limit(5)
+        with pytest.raises(mt.MotifsError) as err:
+            mt.count_host(dg, t5)
+        assert err.value.status == mt.MT_ETIMEOUT
+    finally:
+        mt.set_wait_limit(0)
+    np.testing.assert_array_equal(mt.count_host(dg, t5), want)
