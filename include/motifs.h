@@ -267,8 +267,8 @@ mt_status mt_workspace_query(const mt_graph* g, int k, size_t* bytes);
  * and waits for work handed over by the other warps of its block (the wait is
  * also bounded by a poll count).  When it expires the warp stops and the count
  * reports MT_ETIMEOUT (its histogram is then incomplete).  Applies to the
- * launches enqueued after the call, process-wide; 0 restores the default of
- * 60 s.  A fault-injection hook: a limit of a few nanoseconds makes any count
+ * launches enqueued after the call, process-wide (a batch replays the limit in
+ * force when its step was captured); 0 restores the default of 60 s.  A fault-injection hook: a limit of a few nanoseconds makes any count
  * whose warps go idle at different times report MT_ETIMEOUT, without a GPU
  * fault or hang.  The paper has no counterpart. */
 mt_status mt_set_wait_limit(uint64_t ns);
