@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "count.cuh"
+#include "trace.cuh"
 
 namespace mt {
 cudaError_t launch_randomize(int32_t n, int32_t m, int G, const int32_t* row_ptr,
@@ -339,6 +340,7 @@ mt_status mt_batch_free(mt_batch* b) {
 mt_status mt_batch_run(mt_batch* b, const uint64_t* seeds, uint64_t* hists, double* z,
                        void* stream) {
   if (!b || !seeds) return MT_EINVAL;
+  TraceRange tr("mt_batch_run");
   return batch_run(b, seeds, hists, z, (cudaStream_t)stream);
 }
 
@@ -364,6 +366,7 @@ mt_status mt_batch_error(const mt_batch* b, uint32_t* err) {
 
 mt_status mt_count_batch(const mt_graph* g, const mt_table* t, const uint64_t* seeds, int R,
                          uint64_t swaps, uint64_t* hists, double* z, void* stream) {
+  TraceRange tr("mt_count_batch");
   mt_batch* b = nullptr;
   MT_TRY(mt_batch_create(g, t, R, swaps, &b));
   mt_status st = mt_batch_run(b, seeds, hists, z, stream);

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "trace.cuh"
 
 namespace mt {
 
@@ -318,6 +319,7 @@ const char* mt_last_error(void) { return g_last_error.c_str(); }
 mt_status mt_graph_load_csr(int32_t n, int32_t m, const int32_t* row_ptr, const int32_t* col,
                             void* stream, mt_graph** out) {
   if (!out) return MT_EINVAL;
+  TraceRange tr("mt_graph_load_csr");
   return graph_load_impl(n, m, row_ptr, col, false, (cudaStream_t)stream, out);
 }
 

@@ -18,6 +18,7 @@
 // generator): state advances by the golden gamma 0x9E3779B97F4A7C15, output =
 // mix(state) with the variant-13 mix; output i of seed s is mix(s + (i+1)*gamma).
 #include "graph.cuh"
+#include "trace.cuh"
 
 namespace mt {
 
@@ -368,6 +369,7 @@ extern "C" {
 mt_status mt_randomize(const mt_graph* src, uint64_t seed, uint64_t swaps, void* stream,
                        mt_graph** out) {
   if (!src || !out) return MT_EINVAL;
+  TraceRange tr("mt_randomize");
   cudaStream_t s = (cudaStream_t)stream;
   mt_graph* g = nullptr;
   MT_TRY(graph_alloc(src->n, src->m, &g));
@@ -404,6 +406,7 @@ mt_status mt_randomize(const mt_graph* src, uint64_t seed, uint64_t swaps, void*
 mt_status mt_randomize_dyads(const mt_graph* src, uint64_t seed, uint64_t attempts, void* stream,
                              mt_graph** out) {
   if (!src || !out) return MT_EINVAL;
+  TraceRange tr("mt_randomize_dyads");
   cudaStream_t s = (cudaStream_t)stream;
   if (rand_smem_bytes(src->m) > 200 * 1024) return MT_EUNSUPPORTED;
   mt_graph* g = nullptr;

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "count.cuh"
+#include "trace.cuh"
 
 namespace mt {
 
@@ -425,6 +426,7 @@ mt_status mt_server_submit(mt_server* s, int k, int32_t n, int32_t m, const int3
 
 mt_status mt_server_step(mt_server* s, int32_t* completed, int32_t* active, int32_t* pending) {
   if (!s) return MT_EINVAL;
+  TraceRange tr("mt_server_step");
   int32_t done = 0;
   mt_status st = step(s, &done);
   if (completed) *completed = done;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "trace.cuh"
 
 struct mt_table {
   int k = 0;
@@ -480,12 +481,14 @@ extern "C" {
 mt_status mt_table_build(int k, void* stream, mt_table** out) {
   if (!out) return MT_EINVAL;
   if (k < 3 || k > 6) return MT_EUNSUPPORTED;
+  TraceRange tr("mt_table_build");
   return build_table(k, (cudaStream_t)stream, out);
 }
 
 mt_status mt_table_build_compact(int k, void* stream, mt_table** out) {
   if (!out) return MT_EINVAL;
   if (k != 6) return MT_EUNSUPPORTED;
+  TraceRange tr("mt_table_build_compact");
   return build_compact6((cudaStream_t)stream, out);
 }
 
