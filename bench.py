@@ -172,20 +172,31 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _captured_traffic(method, workload, nulls):
-    """DRAM bytes per k_count launch from the committed ncu summary
-    (profiles/k_count_traffic.md), only if it was captured from the current
-    kernel source and the same launch; else None."""
-    path = os.path.join(ROOT, "profiles", "k_count_traffic.md")
-    if not os.path.exists(path):
+COUNTERS_JSON = os.path.join(ROOT, "profiles", "k_count_counters.json")
+
+
+def _captured(kind, method, workload, nulls):
+    """An ncu capture of one k_count launch recorded in profiles/k_count_counters.json
+    (entries keyed by what was captured: `kind` "traffic" for the full-size DRAM
+    bytes, "gather" for the small-case load and reduction counters), only if it
+    was taken from the current kernel source and the same launch; else None."""
+    if not os.path.exists(COUNTERS_JSON):
         return None
-    want = f"traffic method={method} workload={workload} nulls={nulls} source={_kernel_source_hash()}"
-    with open(path) as f:
-        for line in f:
-            line = line.strip().strip("`")
-            if line.startswith(want + " bytes="):
-                return int(line.split("bytes=")[1])
+    with open(COUNTERS_JSON) as f:
+        entries = json.load(f).get("captures", [])
+    src = _kernel_source_hash()
+    for e in entries:
+        if (e.get("kind") == kind and e.get("method") == method and e.get("workload") == workload
+                and e.get("nulls") == nulls and e.get("source") == src):
+            return e
     return None
+
+
+def _captured_traffic(method, workload, nulls):
+    """DRAM bytes per k_count launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of a full-size capture of the current kernel, else None."""
+    e = _captured("traffic", method, workload, nulls)
+    return None if e is None else int(e["dram_bytes"])
 
 
 def _config(args, w, world):
@@ -348,7 +359,8 @@ def run_ours(args, world, rank, local):
 
     peaks, src = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # Tops/s
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # Tops/s
     roofline = None
     if R and count_ms:
         cm = statistics.mean(count_ms)
@@ -359,14 +371,16 @@ def run_ours(args, world, rank, local):
                     "traffic": _captured_traffic(args.method, args.workload, R),
                     "kernel": "k_count (enumerate+classify+count)", "kernel_ms": cm,
                     "ops_per_subgraph": ops_per_subgraph(k),
-                    "peak_source": f"152 SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_mhz} MHz "
-                                   f"({src} sm_max_mhz)"}
+                    "peak_source": f"{sms} SMs (device query) x {INT32_LANES_PER_SM} int32 lanes "
+                                   f"x {sm_mhz} MHz ({src} sm_max_mhz)"}
 
     extra = {}
     if (rank == 0 and not args.no_extra and args.workload == "nullmodel_k5" and args.nulls is None
             and args.method == "enumerate"):
         extra["plain_vs_batched"] = measure_plain_vs_batched(
             mt, torch, dg, table, g, (1 + R) / (total_ms / args.steps / 1000.0))
+        extra["k3_uniform_latency"] = measure_single("uniform_k3", mt, torch)
+        extra["k4_chunglu_plain"] = measure_single("chunglu_k4", mt, torch)
         extra["k6_batch"] = measure_k6(mt, torch)
         dyad = measure_batch_method(mt, torch, "nullmodel_k5", table, method=0, null_model=1)
         dyad["metric"] = "k-subgraphs classified/s"
@@ -383,7 +397,7 @@ def run_ours(args, world, rank, local):
     gar = None
     if rank == 0 and R and count_ms:
         sub_rate = subgraphs_per_step / (statistics.mean(count_ms) / 1000.0)
-        gar = _ceilings(mt, k, sub_rate)
+        gar = _ceilings(mt, k, sub_rate, args.method, args.workload)
 
     if rank == 0:
         line = {"metric": "k-subgraphs classified/s", "value": value, "unit": "subgraphs/s",
@@ -420,30 +434,95 @@ def _timed(torch, fn, steps, flush):
     return total
 
 
-def _ceilings(mt, k, sub_rate):
-    """The count kernel's rate against the measured ceilings of one random
-    table read (table of 2^(k(k-1)) words, as the k-vertex table) and one
-    random 64-bit histogram add (counters: the class count rounded up to a
-    power of two) per classified subgraph."""
+def _ceilings(mt, k, sub_rate, method="enumerate", workload=None):
+    """The count kernel's global-memory work against the measured ceilings of
+    random 4 B reads from a table of 2^(k(k-1)) words (the k-vertex table) and
+    random 64-bit atomic adds into the class count's power of two of counters.
+
+    The kernel does not read the table once per subgraph: it reads once per
+    group of equal keys.  So the reads and reductions it actually issues per
+    classified subgraph come from an ncu capture of the current kernel
+    (global-load and global-reduction sectors of one small-case launch,
+    profiles/k_count_counters.json), and the fraction is issued sectors/s over
+    the probe's random reads/s (each probe read touches one sector)."""
     table_words = 1 << (k * (k - 1))
     hist_words = 1 << (int(syn_classes(k)) - 1).bit_length()
     gps, aps = mt.probe_rates(table_words, hist_words)
-    return {"gather_peak_per_s": gps, "atomic_peak_per_s": aps,
-            "kernel_subgraphs_per_s": sub_rate, "frac_of_gather": sub_rate / gps,
-            "frac_of_atomic": sub_rate / aps, "table_bytes": 4 * table_words,
-            "hist_counters": hist_words,
-            "note": "per-subgraph ceilings: one random 4 B read from the k-vertex table and one "
-                    "random 64-bit atomic add per classified subgraph (mt_probe_rates, measured "
-                    "in this run); grouping equal keys and cache locality let the kernel exceed "
-                    "them"}
+    out = {"gather_peak_per_s": gps, "atomic_peak_per_s": aps,
+           "kernel_subgraphs_per_s": sub_rate, "table_bytes": 4 * table_words,
+           "hist_counters": hist_words}
+    cap = _captured("gather", method, workload, None) if workload else None
+    if cap is None:
+        out["issued"] = None
+        out["note"] = ("no ncu capture of the current kernel for this workload: reads and adds "
+                       "issued per subgraph unknown")
+        return out
+    ld = cap["global_ld_sectors"] / cap["subgraphs"]
+    red = cap["global_red_sectors"] / cap["subgraphs"]
+    out["issued"] = {"global_ld_sectors_per_subgraph": ld, "global_red_sectors_per_subgraph": red,
+                     "global_ld_requests_per_subgraph": cap["global_ld_requests"] / cap["subgraphs"],
+                     "global_red_requests_per_subgraph": cap["global_red_requests"] / cap["subgraphs"],
+                     "capture": cap["case"]}
+    out["frac_of_gather"] = ld * sub_rate / gps
+    out["frac_of_atomic"] = red * sub_rate / aps if red > 0 else 0.0
+    out["note"] = ("issued global-load and global-reduction sectors per classified subgraph "
+                   "(ncu, small case of the same kernel) x the kernel's subgraphs/s, over the "
+                   "measured random-read and random-atomic rates (mt_probe_rates, this run); "
+                   + cap.get("reading", ""))
+    return out
 
 
 def syn_classes(k):
     return {3: 13, 4: 199, 5: 9364, 6: 1530843}[k]
 
 
-def measure_k6(mt, torch, steps=3, warmup=3):
-    """The k=6 null-model batch: Chung-Lu n=800, m=3,200 plus 64 nulls."""
+def measure_single(name, mt, torch, calls=200, warmup=20):
+    """One plain count of a small workload graph, the way a caller makes it:
+    single-call latency (host clock, p50/p99) with the graph resident on the
+    device and the histogram copied to a host buffer, the same end to end from
+    the host CSR (load, count, histogram back, free), and the device-timed rate
+    of the count alone (CUDA events, L2 flushed before each call)."""
+    w = syn.WORKLOADS[name]
+    g = syn.workload_graph(name)
+    t = mt.table_build(w["k"])
+    dg = mt.graph_from(g)
+    out = torch.empty(t.num_classes, dtype=torch.int64, device="cuda")
+    for _ in range(warmup):
+        mt.count_host(dg, t)
+    sub = int(mt.count_host(dg, t).sum())
+    lat = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        mt.count_host(dg, t)
+        lat.append(1000 * (time.perf_counter() - t0))
+    lat_e2e = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        gg = mt.graph_load_csr(g.n, g.row_ptr, g.col)
+        h = mt.count_host(gg, t)
+        gg.free()
+        lat_e2e.append(1000 * (time.perf_counter() - t0))
+    assert int(h.sum()) == sub
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    steps = 20
+    ms = _timed(torch, lambda: mt.count(dg, t, out), steps, flush)
+    res = {"config": f"{name}: n={w['n']} m={w['m']} k={w['k']}", "subgraphs_per_call": sub,
+           "device_subgraphs_per_s": sub * steps / (ms / 1000.0), "device_ms_per_call": ms / steps,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "subgraphs_per_s_at_p50": sub / (np.percentile(lat, 50) / 1000.0),
+           "e2e_p50_ms": float(np.percentile(lat_e2e, 50)),
+           "e2e_p99_ms": float(np.percentile(lat_e2e, 99)),
+           "note": "p50/p99: mt_count into a host buffer on a resident graph (plan, enumerate, copy "
+                   "back, synchronise); e2e: mt_graph_load_csr + mt_count + free per call"}
+    dg.free()
+    t.free()
+    return res
+
+
+def measure_k6(mt, torch, steps=3, warmup=3, nplain=16):
+    """The k=6 null-model batch: Chung-Lu n=800, m=3,200 plus 64 nulls; and the
+    plain path on the same kind of graphs (one mt_count launch per graph: the
+    original and `nplain` nulls made beforehand by mt_randomize)."""
     w = syn.WORKLOADS["nullmodel_k6"]
     g = syn.workload_graph("nullmodel_k6")
     t0 = time.perf_counter()
@@ -470,10 +549,14 @@ def measure_k6(mt, torch, steps=3, warmup=3):
            "graphs_per_s": (R + 1) * steps / (ms / 1000.0), "ms_per_step": ms / steps,
            "count_kernel_ms": cm, "subgraphs_per_step": sub, "graphs_per_step": R + 1,
            "table_build_ms": table_ms,
-           "gather_atomic_roofline": _ceilings(mt, 6, sub / (cm / 1000.0)),
+           "gather_atomic_roofline": _ceilings(mt, 6, sub / (cm / 1000.0), "enumerate",
+                                               "nullmodel_k6"),
            "config": "Chung-Lu n=800 m=3200 gamma 2.5 dmax 40 r 0.10 + 64 nulls, k=6"}
     ref = mt.to_numpy_u64(hists).copy()
     b.free()
+    # plain: one launch per graph on the same table
+    out["plain_vs_batched"] = measure_plain_vs_batched(mt, torch, dg, t, g, out["graphs_per_s"],
+                                                       nplain)
     t.free()
     # the same batch with the compact k = 6 table (208 MB instead of 4 GiB)
     t0 = time.perf_counter()

@@ -242,10 +242,25 @@ mt_status mt_count_tuned(const mt_graph* g, const mt_table* t, uint64_t* hist,
  *   before any stream capture.
  * - All calls share the one array: calls that overlap on the GPU (other
  *   streams or host threads) race and give wrong counts.  Serialise them.
- * - Errors: MT_EINVAL (null handle, or hist not device memory),
- *   MT_EUNSUPPORTED when the graph needs more scratch than the array holds
- *   (mt_last_error() gives both sizes; use mt_count), MT_ECUDA. */
+ * - The call returns once the work is enqueued, before the kernels run, so it
+ *   cannot report what they find (a stack or queue overflow, an expired idle
+ *   wait).  Their status word stays in the fixed array until the next call:
+ *   read it with mt_count_noalloc_error after the count, before the next
+ *   mt_count_noalloc.  A non-zero word means the histogram is invalid.
+ * - Errors: MT_EINVAL (null handle, hist not device memory, or hist on
+ *   another device than the current one), MT_EUNSUPPORTED when the graph
+ *   needs more scratch than the array holds (mt_last_error() gives both
+ *   sizes; use mt_count), MT_ECUDA. */
 mt_status mt_count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* hist, void* stream);
+
+/* Status of the last mt_count_noalloc on the current device (the paper has
+ * no counterpart).  Waits for `stream` (the stream of that count), copies the
+ * device status word out of the fixed array into *err (HOST, may be NULL;
+ * 0 = the histogram is exact) and returns MT_OK for 0, MT_ETIMEOUT when a
+ * bounded device wait expired (see mt_set_wait_limit), MT_EOVERFLOW for a
+ * stack, queue or class-id bound exceeded; in both cases the histogram is
+ * invalid.  Allocates nothing.  MT_ECUDA if the copy fails. */
+mt_status mt_count_noalloc_error(uint32_t* err, void* stream);
 
 /* Caller-provided scratch for the counts of one graph handle (the paper has no
  * counterpart; for callers whose device memory comes from their own allocator,

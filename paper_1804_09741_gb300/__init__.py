@@ -64,6 +64,7 @@ SIGNATURES = {
     "mt_count_tuned": (ctypes.c_int, [_vp, _vp, _vp, _P(Tuning), _vp]),
     "mt_count_stats": (ctypes.c_int, [_vp, _P(_u64), _P(_u32), _P(ctypes.c_float)]),
     "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mt_count_noalloc_error": (ctypes.c_int, [_P(_u32), _vp]),
     "mt_workspace_query": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_size_t)]),
     "mt_set_workspace": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "mt_set_wait_limit": (ctypes.c_int, [_u64]),
@@ -302,6 +303,18 @@ def count_noalloc(g: Graph, t: Table, out=None, stream=None):
     _check(_lib.mt_count_noalloc(g.handle, t.handle, out.data_ptr(), _stream(stream)),
            "mt_count_noalloc")
     return out
+
+
+def count_noalloc_error(stream=None) -> int:
+    """Status word of the last count_noalloc on this device (waits for the
+    stream; 0 = exact).  Raises MotifsError (MT_ETIMEOUT / MT_EOVERFLOW) when
+    the word is non-zero, i.e. the histogram is invalid."""
+    err = _u32()
+    st = _lib.mt_count_noalloc_error(ctypes.byref(err), _stream(stream))
+    if st in (MT_ETIMEOUT, MT_EOVERFLOW):
+        raise MotifsError(st, "mt_count_noalloc_error", f"status word {err.value:#x}")
+    _check(st, "mt_count_noalloc_error")
+    return int(err.value)
 
 
 def workspace_query(g: Graph, k: int) -> int:

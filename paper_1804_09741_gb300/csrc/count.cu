@@ -1293,6 +1293,15 @@ static mt_status count_one(const mt_graph* gc, const mt_table* t, uint64_t* hist
   bool dev_hist = cudaPointerGetAttributes(&attr, hist) == cudaSuccess &&
                   (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
   cudaGetLastError();
+  if (dev_hist && attr.type == cudaMemoryTypeDevice) {
+    int dev = 0;
+    MT_CUDA_TRY(cudaGetDevice(&dev));
+    if (attr.device != dev) {  // this device's kernels would write another GPU's memory
+      set_last_error("hist is memory of device " + std::to_string(attr.device) +
+                     ", the current device is " + std::to_string(dev));
+      return MT_EINVAL;
+    }
+  }
   unsigned long long* dh =
       dev_hist ? (unsigned long long*)hist : (unsigned long long*)(base + p.ws_bytes + 256);
   DevGraph hg = dev_view(g, dh);

@@ -61,7 +61,9 @@ mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
                         cudaStream_t s);
 
 // Read the launch's error word and item count from the workspace (device
-// pointers into `ws`).
+// pointers into `ws`).  The header holding the error word is at offset 0 of
+// every plan's workspace, so the error word's address does not depend on the
+// plan.
 uint32_t* count_err_ptr(const CountPlan& p, void* ws);
 uint32_t* count_nitems_ptr(const CountPlan& p, void* ws);
 

@@ -14,6 +14,10 @@
 // library reserves it until the process exits.  All calls share it, so calls
 // that overlap on the GPU (different streams, different threads) race and give
 // wrong counts: order them on one stream or synchronise between them.
+//
+// The launch's status word (stack or queue overflow, an expired idle wait)
+// stays in the array's header until the next call; mt_count_noalloc_error
+// copies it out, because the count itself returns before the kernels run.
 #include <mutex>
 
 #include "count.cuh"
@@ -55,11 +59,19 @@ __global__ void k_put_graph(DevGraph* dst, DevGraph src) { *dst = src; }
 
 static mt_status count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* hist,
                                cudaStream_t s) {
+  int dev = 0;
+  MT_CUDA_TRY(cudaGetDevice(&dev));
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, hist) != cudaSuccess ||
       (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
     cudaGetLastError();
     set_last_error("mt_count_noalloc: hist must be device memory");
+    return MT_EINVAL;
+  }
+  if (attr.type == cudaMemoryTypeDevice && attr.device != dev) {
+    // this device's kernels would write another GPU's memory
+    set_last_error("mt_count_noalloc: hist is memory of device " + std::to_string(attr.device) +
+                   ", the current device is " + std::to_string(dev));
     return MT_EINVAL;
   }
   void* scratch = nullptr;
@@ -81,11 +93,34 @@ static mt_status count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* h
   k_put_graph<<<1, 1, 0, s>>>(dg, dev_view(g, (unsigned long long*)hist));
   MT_CUDA_TRY(cudaGetLastError());
   MT_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)C * 8, s));
-  if (g->n >= K) MT_TRY(count_enqueue(p, scratch, dg, table_view(t), 0, g->n, s));
+  if (g->n >= K) {
+    MT_TRY(count_enqueue(p, scratch, dg, table_view(t), 0, g->n, s));
+  } else {
+    // no launch: clear the status word a previous call left behind
+    MT_CUDA_TRY(cudaMemsetAsync(count_err_ptr(p, scratch), 0, 4, s));
+  }
   return MT_OK;
 }
 
+// Status word of the last count that used the fixed scratch: its planner and
+// enumerator write their error bits into the header at the start of the array.
+static mt_status noalloc_error(uint32_t* err, cudaStream_t s) {
+  void* scratch = nullptr;
+  MT_TRY(scratch_address(&scratch));
+  uint32_t word = 0;
+  MT_CUDA_TRY(cudaMemcpyAsync(&word, count_err_ptr(CountPlan{}, scratch), 4,
+                              cudaMemcpyDeviceToHost, s));
+  MT_CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) *err = word;
+  if (word == 0) return MT_OK;
+  return (word & kErrWaitLimit) ? MT_ETIMEOUT : MT_EOVERFLOW;
+}
+
 }  // namespace mt
+
+extern "C" mt_status mt_count_noalloc_error(uint32_t* err, void* stream) {
+  return mt::noalloc_error(err, (cudaStream_t)stream);
+}
 
 extern "C" mt_status mt_count_noalloc(const mt_graph* g, const mt_table* t, uint64_t* hist,
                                       void* stream) {

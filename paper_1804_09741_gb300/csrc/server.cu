@@ -17,6 +17,13 @@
 //  * a request whose last chunk ran is complete when its round's event fires:
 //    its histogram was copied to a pinned buffer behind the kernels, its device
 //    memory goes back to the pool and its slot frees up for the next admission.
+//    Each k's launch also copies its device status word out; a request any of
+//    whose chunks ran in a launch that reported an error (an expired bounded
+//    wait, a stack or queue bound) fails with that error instead of returning
+//    a histogram that may be incomplete;
+//  * the budget covers the requests' memory and the per-k round scratch
+//    (planner, work queue, graph descriptors): a request is admitted only if
+//    the scratch its k would need with it active still fits.
 // Rounds are double-buffered: the host admits and plans round r+1 while the GPU
 // runs round r, so requests that arrive mid-round join the next round instead
 // of waiting for whole requests ahead of them to finish.
@@ -38,6 +45,9 @@ struct SrvRequest {
   int32_t n = 0, m = 0;
   std::vector<int32_t> rp, col;  // host copy until admitted
   std::vector<double> cum;       // cumulative per-root cost estimate (n+1)
+  int32_t dmax_b = 0;            // bounds for planning before the device build:
+  int32_t nu_b = 0;              //   largest in+out degree, 2m undirected entries
+  uint32_t taint = 0;            // device error bits of launches its chunks ran in
   mt_graph* g = nullptr;
   unsigned long long* d_hist = nullptr;
   uint64_t* h_result = nullptr;  // pinned
@@ -51,6 +61,8 @@ struct SrvRequest {
 struct RoundBuf {
   cudaEvent_t ev = nullptr;
   std::vector<SrvRequest*> finishing;
+  std::vector<SrvRequest*> chunked[4];  // requests with a chunk in this round, per k
+  uint32_t* h_err = nullptr;            // pinned: each k's launch status word
   DevGraph* h_graphs = nullptr;  // pinned staging of the round's graph descriptors
   size_t h_cap = 0;
   bool pending = false;
@@ -77,6 +89,7 @@ struct mt_server {
   size_t ws_bytes[4] = {0, 0, 0, 0};
   mt::DevGraph* d_graphs[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t d_graphs_cap[4] = {0, 0, 0, 0};
+  size_t reserved[4] = {0, 0, 0, 0};  // round scratch charged to the budget, per k
   std::vector<uint64_t*> pinned_free[4];  // result buffers by k
   std::chrono::steady_clock::time_point t0;
   int method = MT_METHOD_ENUMERATE;
@@ -103,6 +116,9 @@ static void root_costs(SrvRequest* r) {
   std::vector<int32_t> deg(n, 0);
   for (int v = 0; v < n; ++v) deg[v] += r->rp[v + 1] - r->rp[v];
   for (int32_t e = 0; e < r->m; ++e) deg[r->col[e]] += 1;
+  r->dmax_b = 1;
+  for (int v = 0; v < n; ++v) r->dmax_b = std::max(r->dmax_b, deg[v]);
+  r->nu_b = std::max(2 * r->m, 1);
   std::vector<double> cost(n, 1.0);
   for (int v = 0; v < n; ++v)
     for (int32_t e = r->rp[v]; e < r->rp[v + 1]; ++e) {
@@ -117,6 +133,54 @@ static void root_costs(SrvRequest* r) {
 static size_t request_bytes(const SrvRequest* r, uint32_t C) {
   // graph arrays + histogram + a planner/work-item share per arc
   return graph_device_bytes(r->n, r->m) + (size_t)C * 8 + (size_t)64 * (r->m + r->n) + 4096;
+}
+
+// Launch plan of one k's round over the active requests of that k (plus
+// `extra`, when given): the round's chunks are a subset of them, and a
+// request's degree bound and 2m bound its device graph's, so the scratch of
+// any round is at most this plan's.
+static mt_status plan_for(const mt_server* s, int ki, const SrvRequest* extra, CountPlan* p,
+                          int* G) {
+  int nmax = 1, dmax = 1, numax = 1, g = 0;
+  int64_t fwd = 0;
+  auto add = [&](const SrvRequest* r) {
+    nmax = std::max(nmax, r->n);
+    dmax = std::max(dmax, r->dmax_b);
+    numax = std::max(numax, r->nu_b);
+    fwd += r->nu_b / 2 + 1;
+    ++g;
+  };
+  for (const SrvRequest* r : s->active)
+    if (r->k == ki + 3) add(r);
+  if (extra) add(extra);
+  *G = g;
+  if (g == 0) return MT_OK;
+  mt_tuning tun;
+  tun.split_cost = 0.0;
+  tun.split_scale = 0.0;
+  tun.warps_per_block = 0;
+  tun.stack_cap = 0;
+  tun.method = s->method;
+  return count_configure_tuned(p, ki + 3, g, nmax, dmax, fwd, numax,
+                               table_classes(s->tables[ki]),
+                               s->method == MT_METHOD_ENUMERATE ? nullptr : &tun,
+                               table_compact(s->tables[ki]));
+}
+
+// Round scratch of k's launch (planner and work queue, graph descriptors) for
+// the active requests of k plus `extra`; 0 when there are none or when the
+// launch cannot be configured (such requests fail in the round, unscheduled).
+static size_t scratch_need(const mt_server* s, int ki, const SrvRequest* extra) {
+  CountPlan p;
+  int G = 0;
+  if (plan_for(s, ki, extra, &p, &G) != MT_OK || G == 0) return 0;
+  return p.ws_bytes + (size_t)G * sizeof(DevGraph);
+}
+
+static size_t reserved_total(const mt_server* s) {
+  size_t t = 0;
+  for (size_t x : s->reserved) t += x;
+  return t;
 }
 
 static mt_status acquire_pinned(mt_server* s, int k, uint32_t C, uint64_t** out) {
@@ -165,7 +229,17 @@ static void admit(mt_server* s) {
       r->t_done = now_ms(s);
       continue;
     }
-    if (s->used + r->bytes > s->budget) break;
+    // the scratch r's k needs with r active, against what k holds now
+    const int ki = r->k - 3;
+    const size_t need_k = std::max(s->reserved[ki], scratch_need(s, ki, r));
+    if (r->bytes + need_k > s->budget) {  // can never fit, even alone
+      s->pending.pop_front();
+      r->state = 3;
+      r->status = MT_EBUSY;
+      r->t_done = now_ms(s);
+      continue;
+    }
+    if (s->used + r->bytes + reserved_total(s) - s->reserved[ki] + need_k > s->budget) break;
     s->pending.pop_front();
     mt_status st = graph_load_on(r->n, r->m, r->rp.data(), r->col.data(), s->load_stream, &r->g);
     if (st == MT_OK) st = acquire_pinned(s, r->k, C, &r->h_result);
@@ -190,6 +264,7 @@ static void admit(mt_server* s) {
     std::vector<int32_t>().swap(r->rp);
     std::vector<int32_t>().swap(r->col);
     s->used += r->bytes;
+    s->reserved[ki] = need_k;
     r->state = 1;
     r->t_admit = now_ms(s);
     r->next_root = 0;
@@ -202,6 +277,9 @@ static void admit(mt_server* s) {
   }
 }
 
+// Grow k's round scratch to this round's plan.  The admitted requests' plan
+// bounds it, so what is allocated stays within the reservation charged to the
+// budget.
 static mt_status ensure_capacity(mt_server* s, int ki, size_t ws_need, size_t graphs) {
   if (s->ws_bytes[ki] < ws_need) {
     if (s->ws[ki]) MT_CUDA_TRY(cudaFreeAsync(s->ws[ki], s->stream));
@@ -212,26 +290,57 @@ static mt_status ensure_capacity(mt_server* s, int ki, size_t ws_need, size_t gr
   }
   if (s->d_graphs_cap[ki] < graphs) {
     if (s->d_graphs[ki]) MT_CUDA_TRY(cudaFreeAsync(s->d_graphs[ki], s->stream));
-    const size_t cap = std::max<size_t>(graphs, 2 * s->d_graphs_cap[ki]);
+    const size_t cap = graphs;
     MT_CUDA_TRY(cudaMallocAsync((void**)&s->d_graphs[ki], cap * sizeof(DevGraph), s->stream));
     s->d_graphs_cap[ki] = cap;
   }
   return MT_OK;
 }
 
+// Free k's round scratch once no active request of k is left (stream-ordered
+// behind every launch enqueued so far) and drop its reservation.
+static void release_idle_scratch(mt_server* s) {
+  for (int ki = 0; ki < 4; ++ki) {
+    bool any = false;
+    for (const SrvRequest* r : s->active) any |= r->k == ki + 3;
+    if (any) continue;
+    if (s->ws[ki]) cudaFreeAsync(s->ws[ki], s->stream);
+    if (s->d_graphs[ki]) cudaFreeAsync(s->d_graphs[ki], s->stream);
+    s->ws[ki] = nullptr;
+    s->ws_bytes[ki] = 0;
+    s->d_graphs[ki] = nullptr;
+    s->d_graphs_cap[ki] = 0;
+    s->reserved[ki] = 0;
+  }
+}
+
 static mt_status harvest(mt_server* s, RoundBuf& b, int32_t* completed) {
   if (!b.pending) return MT_OK;
   MT_CUDA_TRY(cudaEventSynchronize(b.ev));
   const double t = now_ms(s);
+  // a launch that reported an error taints every request it ran a chunk of
+  for (int ki = 0; ki < 4; ++ki) {
+    if (b.h_err[ki])
+      for (SrvRequest* r : b.chunked[ki]) r->taint |= b.h_err[ki];
+    b.chunked[ki].clear();
+  }
   for (SrvRequest* r : b.finishing) {
-    r->state = 2;
+    release_request(s, r);  // while still active: its budget charge is returned
+    if (r->taint) {
+      r->state = 3;
+      r->status = (r->taint & kErrWaitLimit) ? MT_ETIMEOUT : MT_EOVERFLOW;
+      if (r->h_result) s->pinned_free[r->k - 3].push_back(r->h_result);
+      r->h_result = nullptr;
+    } else {
+      r->state = 2;
+      ++*completed;
+    }
     r->t_done = t;
-    release_request(s, r);
     s->active.erase(std::find(s->active.begin(), s->active.end(), r));
-    ++*completed;
   }
   b.finishing.clear();
   b.pending = false;
+  release_idle_scratch(s);
   return MT_OK;
 }
 
@@ -277,6 +386,7 @@ static mt_status step(mt_server* s, int32_t* completed) {
         b = std::min(b, r->n);
       }
       by_k[r->k - 3].push_back({r, a, b});
+      R.chunked[r->k - 3].push_back(r);
       r->next_root = b;
       if (b == r->n) R.finishing.push_back(r);
     }
@@ -317,6 +427,9 @@ static mt_status step(mt_server* s, int32_t* completed) {
           count_configure_tuned(&p, K, (int)chunks.size(), nmax, dmax, fwd, numax, C,
                                 s->method == MT_METHOD_ENUMERATE ? nullptr : &tun, table_compact(t));
       if (cst == MT_OK) cst = ensure_capacity(s, ki, p.ws_bytes, chunks.size());
+      if (cst == MT_OK)  // charge what is held, should the plan outgrow the reservation
+        s->reserved[ki] = std::max(s->reserved[ki],
+                                   s->ws_bytes[ki] + s->d_graphs_cap[ki] * sizeof(DevGraph));
       if (cst != MT_OK) {
         // this k cannot run (its table and the server's method do not go
         // together, e.g. the cell method on a compact k = 6 table, or its
@@ -324,6 +437,7 @@ static mt_status step(mt_server* s, int32_t* completed) {
         // of their roots is marked as counted
         for (auto& c : chunks) fail_request(s, R, c.r, cst);
         chunks.clear();
+        R.chunked[ki].clear();
         cudaGetLastError();  // an allocation failure is not sticky: clear it
         continue;
       }
@@ -342,11 +456,14 @@ static mt_status step(mt_server* s, int32_t* completed) {
     // fork: each k's launch waits for what the main stream holds (loads,
     // allocations, descriptors, the previous round), then joins back
     MT_CUDA_TRY(cudaEventRecord(s->fork_ev, s->stream));
+    for (int ki = 0; ki < 4; ++ki) R.h_err[ki] = 0;  // this buffer's last round was harvested
     for (int ki = 0; ki < 4; ++ki) {
       if (by_k[ki].empty()) continue;
       MT_CUDA_TRY(cudaStreamWaitEvent(s->kstream[ki], s->fork_ev, 0));
       MT_TRY(count_enqueue(plans[ki], s->ws[ki], s->d_graphs[ki], table_view(s->tables[ki]), 0,
                            nmaxs[ki], s->kstream[ki]));
+      MT_CUDA_TRY(cudaMemcpyAsync(R.h_err + ki, count_err_ptr(plans[ki], s->ws[ki]), 4,
+                                  cudaMemcpyDeviceToHost, s->kstream[ki]));
       MT_CUDA_TRY(cudaEventRecord(s->kdone_ev[ki], s->kstream[ki]));
       MT_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->kdone_ev[ki], 0));
     }
@@ -388,8 +505,11 @@ mt_status mt_server_create(const mt_table* t3, const mt_table* t4, const mt_tabl
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->load_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->load_ev, cudaEventDisableTiming);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&s->rb[i].ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->rb[i].h_err, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) std::fill(s->rb[i].h_err, s->rb[i].h_err + 4, 0u);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
     e = cudaStreamCreateWithFlags(&s->kstream[i], cudaStreamNonBlocking);
@@ -468,7 +588,7 @@ mt_status mt_server_set_method(mt_server* s, int method) {
 
 mt_status mt_server_used_bytes(const mt_server* s, size_t* used) {
   if (!s || !used) return MT_EINVAL;
-  *used = s->used;
+  *used = s->used + reserved_total(s);
   return MT_OK;
 }
 
@@ -492,6 +612,7 @@ mt_status mt_server_free(mt_server* s) {
   for (auto& b : s->rb) {
     if (b.ev) cudaEventDestroy(b.ev);
     if (b.h_graphs) cudaFreeHost(b.h_graphs);
+    if (b.h_err) cudaFreeHost(b.h_err);
   }
   if (s->load_ev) cudaEventDestroy(s->load_ev);
   if (s->fork_ev) cudaEventDestroy(s->fork_ev);

@@ -19,3 +19,26 @@ def test_strip_comments_keeps_code_changes_and_literals():
 def test_kernel_source_hash_is_stable():
     h = bench._kernel_source_hash()
     assert len(h) == 16 and h == bench._kernel_source_hash()
+
+
+def test_captured_counters_apply_only_to_the_current_source(tmp_path, monkeypatch):
+    import json
+    src = bench._kernel_source_hash()
+    p = tmp_path / "c.json"
+    p.write_text(json.dumps({"captures": [
+        {"kind": "traffic", "method": "enumerate", "workload": "w", "nulls": 4, "source": src,
+         "dram_bytes": 123},
+        {"kind": "traffic", "method": "enumerate", "workload": "w", "nulls": 8,
+         "source": "0000000000000000", "dram_bytes": 456}]}))
+    monkeypatch.setattr(bench, "COUNTERS_JSON", str(p))
+    assert bench._captured_traffic("enumerate", "w", 4) == 123
+    assert bench._captured_traffic("enumerate", "w", 8) is None  # another kernel source
+    assert bench._captured_traffic("cells", "w", 4) is None
+
+
+def test_committed_counters_file_is_valid_json():
+    import json
+    with open(bench.COUNTERS_JSON) as f:
+        d = json.load(f)
+    for e in d["captures"]:
+        assert {"kind", "method", "workload", "source"} <= set(e)

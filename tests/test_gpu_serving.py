@@ -78,12 +78,24 @@ def test_late_small_requests_overtake_a_long_one(tables):
 
 
 def test_budget_and_slots_bound_admission(tables):
+    """The budget covers the requests' memory and their k's round scratch
+    (planner, work queue, graph descriptors): with room for two requests plus
+    the scratch of a two-request round, at most two run at once, the charge
+    never exceeds the budget, and it returns to zero when all are done."""
     import paper_1804_09741_gb300 as mt
     from paper_1804_09741_gb300.server import Server, run_stream
     graphs = [syn.chung_lu_digraph(800, 3000, 2.4, 40, 0.1, 70 + i) for i in range(6)]
-    # room for about two requests at a time
-    per = 4 * (3 * 801 + 5 * 3000) + 64 * 3800 + 13 * 8 + 8192
-    srv = Server(tables, memory_budget=2 * per + 1000, max_slots=3, round_cost=1e6)
+    # request bytes as the server charges them: graph arrays, histogram, planner share
+    per = 4 * (3 * 801 + 5 * 3000) + 64 * 3800 + 13 * 8 + 4096
+    probe = Server(tables, memory_budget=1 << 34, max_slots=2, round_cost=1e6)
+    for g in graphs[:2]:
+        probe.submit(3, g)
+    probe.step()
+    two = probe.used_bytes()
+    assert two > 2 * per  # the round scratch is charged beside the requests
+    probe.free()
+    budget = two + 1000
+    srv = Server(tables, memory_budget=budget, max_slots=3, round_cost=1e6)
     ids = [srv.submit(3, g) for g in graphs]
     seen_pending, max_active = False, 0
     remaining = set(ids)
@@ -92,13 +104,14 @@ def test_budget_and_slots_bound_admission(tables):
         c, a, p = srv.step()
         max_active = max(max_active, a)
         seen_pending |= p > 0
-        assert srv.used_bytes() <= 2 * per + 1000
+        assert srv.used_bytes() <= budget
         for rid in list(remaining):
             st, h, ms, _ = srv.result(rid, 3)
             if st == 2:
                 res[rid] = h
                 remaining.discard(rid)
     assert seen_pending and max_active <= 2
+    assert srv.used_bytes() == 0  # scratch of an idle k is released
     for rid, g in zip(ids, graphs):
         np.testing.assert_array_equal(res[rid], alone(mt, tables[3], g))
     # a request that can never fit the budget fails on its own
@@ -107,6 +120,30 @@ def test_budget_and_slots_bound_admission(tables):
         srv.step()
     st, h, ms, status = srv.result(bid, 6)
     assert st == 3 and status == mt.MT_EBUSY
+    srv.free()
+
+
+def test_launch_errors_fail_their_requests(tables):
+    """Fault injection from the host (no GPU fault, trap or hang): with an
+    idle-wait limit of a few nanoseconds the rounds' launches report an expired
+    wait, and every request that had a chunk in such a launch fails with
+    MT_ETIMEOUT instead of returning a histogram that may be incomplete; with
+    the limit restored the same requests are served exactly."""
+    import paper_1804_09741_gb300 as mt
+    from paper_1804_09741_gb300.server import Server, run_stream
+    reqs = [(5, syn.workload_graph("nullmodel_k5")), (4, syn.workload_graph("chunglu_k4"))]
+    srv = Server(tables, memory_budget=4 << 30, max_slots=8, round_cost=1e12)
+    try:
+        mt.set_wait_limit(5)
+        out, lat, wall = run_stream(srv, reqs)
+    finally:
+        mt.set_wait_limit(0)
+    assert out[0][0] == 3 and out[0][1] is None and out[0][2] == mt.MT_ETIMEOUT
+    assert srv.used_bytes() == 0
+    out, lat, wall = run_stream(srv, reqs)
+    for (k, g), (st, hist, status) in zip(reqs, out):
+        assert st == 2, status
+        np.testing.assert_array_equal(hist, alone(mt, tables[k], g))
     srv.free()
 
 
