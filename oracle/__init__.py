@@ -73,6 +73,8 @@ def _load():
             lib.oracle_count_roots.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int, i32p,
                                                ctypes.c_int64, ctypes.c_int, u32p, u64p,
                                                ctypes.c_int64, u64p]
+            lib.oracle_count_roots_split.restype = ctypes.c_int64
+            lib.oracle_count_roots_split.argtypes = lib.oracle_count_roots.argtypes
             lib.oracle_count_connected_sets.restype = ctypes.c_uint64
             lib.oracle_count_connected_sets.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int,
                                                         ctypes.c_int]
@@ -169,6 +171,17 @@ def count_roots(g, k: int, roots, nthreads: int | None = None):
     roots = np.ascontiguousarray(roots, dtype=np.int32)
     lib = _load()
     return _hist_call(lib.oracle_count_roots, g.n, _p(rp, ctypes.c_int32),
+                      _p(col, ctypes.c_int32), k, _p(roots, ctypes.c_int32), roots.size,
+                      nthreads or default_threads())
+
+
+def count_roots_split(g, k: int, roots, nthreads: int | None = None):
+    """count_roots with each root's first-level extension steps spread over the
+    threads (for hub roots, whose sets one thread would take minutes to list)."""
+    rp, col = _csr(g)
+    roots = np.ascontiguousarray(roots, dtype=np.int32)
+    lib = _load()
+    return _hist_call(lib.oracle_count_roots_split, g.n, _p(rp, ctypes.c_int32),
                       _p(col, ctypes.c_int32), k, _p(roots, ctypes.c_int32), roots.size,
                       nthreads or default_threads())
 

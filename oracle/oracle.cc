@@ -36,6 +36,7 @@
 // the mix of the new state; output i of seed s is mix(s + (i+1)*gamma).
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -152,19 +153,25 @@ struct Esu {
     while (!ext.empty()) {
       int w = ext.back();
       ext.pop_back();
-      std::vector<int> ext2 = ext;
-      for (int u : g.und[w]) {
-        if (u <= root) continue;
-        bool in_sub = std::find(sub.begin(), sub.end(), u) != sub.end();
-        bool near_sub = false;
-        for (int x : sub)
-          if (g.adjacent(x, u)) near_sub = true;
-        if (!in_sub && !near_sub) ext2.push_back(u);
-      }
-      sub.push_back(w);
-      extend(sub, ext2, root);
-      sub.pop_back();
+      branch(sub, ext, root, w);
     }
+  }
+
+  // One step of the extension: add w to sub, whose remaining extension set is
+  // ext (w already taken out of it), plus w's exclusive neighbours.
+  void branch(std::vector<int>& sub, const std::vector<int>& ext, int root, int w) {
+    std::vector<int> ext2 = ext;
+    for (int u : g.und[w]) {
+      if (u <= root) continue;
+      bool in_sub = std::find(sub.begin(), sub.end(), u) != sub.end();
+      bool near_sub = false;
+      for (int x : sub)
+        if (g.adjacent(x, u)) near_sub = true;
+      if (!in_sub && !near_sub) ext2.push_back(u);
+    }
+    sub.push_back(w);
+    extend(sub, ext2, root);
+    sub.pop_back();
   }
 };
 
@@ -304,6 +311,60 @@ int64_t oracle_count_roots(int32_t n, const int32_t* row_ptr, const int32_t* col
         for (int u : g.und[v])
           if (u > v) ext.push_back(u);
         esu.extend(sub, ext, v);
+      }
+      sets[t] = esu.sets;
+    });
+  for (auto& x : th) x.join();
+  Hist total;
+  uint64_t s = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    for (const auto& kv : hists[t]) total[kv.first] += kv.second;
+    s += sets[t];
+  }
+  if (sets_out) *sets_out = s;
+  return write_hist(total, masks_out, counts_out, cap);
+}
+
+// The same as oracle_count_roots, with the work of one root spread over the
+// threads: the root's first-level extension steps (the i-th vertex taken from
+// its extension set, with the set's remaining prefix) are independent of one
+// another, so each (root, step) pair is a unit handed to the next free thread.
+// Used for roots of very high degree, whose sets one thread would take minutes
+// to enumerate.
+int64_t oracle_count_roots_split(int32_t n, const int32_t* row_ptr, const int32_t* col, int k,
+                                 const int32_t* roots, int64_t nroots, int nthreads,
+                                 uint32_t* masks_out, uint64_t* counts_out, int64_t cap,
+                                 uint64_t* sets_out) {
+  if (k < 2 || k > 6 || n < 0) return -1;
+  Digraph g(n, row_ptr, col);
+  if (nthreads < 1) nthreads = 1;
+  // units: (index into roots, step i); step i takes ext0[size - 1 - i]
+  std::vector<std::pair<int64_t, int>> units;
+  for (int64_t r = 0; r < nroots; ++r) {
+    int v = roots[r];
+    int size = 0;
+    for (int u : g.und[v])
+      if (u > v) ++size;
+    for (int i = 0; i < size; ++i) units.push_back({r, i});
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<Hist> hists(nthreads);
+  std::vector<uint64_t> sets(nthreads, 0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t] {
+      auto perms = all_perms(k);
+      Esu esu{g, k, &perms, &hists[t], 0};
+      for (int64_t j = next++; j < (int64_t)units.size(); j = next++) {
+        int v = roots[units[j].first];
+        std::vector<int> ext0;
+        for (int u : g.und[v])
+          if (u > v) ext0.push_back(u);
+        const int i = units[j].second;
+        const int w = ext0[ext0.size() - 1 - i];
+        std::vector<int> ext(ext0.begin(), ext0.end() - 1 - i);
+        std::vector<int> sub{v};
+        esu.branch(sub, ext, v, w);
       }
       sets[t] = esu.sets;
     });

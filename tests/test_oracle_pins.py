@@ -128,6 +128,9 @@ def test_esu_equals_bruteforce_subsets(k, seed):
     assert s_esu == s_bf
     assert h_esu == h_bf
     assert sum(h_esu.values()) == s_esu
+    # the same enumeration with each root's first-level steps spread over threads
+    h_sp, s_sp = oracle.count_roots_split(g, k, np.arange(g.n), nthreads=3)
+    assert (h_sp, s_sp) == (h_bf, s_bf)
 
 
 def _triad_code_of_mask():
@@ -232,6 +235,18 @@ def test_metamorphic_relations(k):
     assert sr == s1
     mapped = {oracle.canon(k, _transpose_mask(k, c)): v for c, v in h1.items()}
     assert hr == mapped
+
+
+def test_split_roots_match_on_a_hub_graph():
+    """A star with a few extra arcs: every set goes through one root's many
+    first-level steps; the split count equals the closed form and the plain one."""
+    from math import comb
+    d = 40
+    g = syn.out_star(d + 1)
+    for k in (3, 4, 5):
+        h, s = oracle.count_roots_split(g, k, np.arange(g.n), nthreads=4)
+        assert s == comb(d, k - 1) and len(h) == 1
+        assert (h, s) == oracle.count_roots(g, k, np.arange(g.n))
 
 
 def test_count_roots_partitions_the_histogram():
