@@ -205,6 +205,7 @@ def _config(args, w, world):
          "gamma": w.get("gamma"), "dmax": w.get("dmax"), "reciprocity": w.get("recip"),
          "null_graphs": nulls, "swaps_per_null": 10 * w["m"] if nulls else 0,
          "graphs_per_step": 1 + nulls, "parallelism": f"replicas{world}",
+         "null_model": getattr(args, "null_model", "arcswap"),
          "l2": "flushed between timed steps (256 MiB write)", "method": args.method}
     if getattr(args, "compact_table", False):
         c["table"] = "compact (199 x 2^18 slots)"
@@ -253,8 +254,9 @@ def run_ours(args, world, rank, local):
                  "stack_cap": tp.stack_cap, "probe_count_ms": tp.ms,
                  "tune_s": time.perf_counter() - t_tune,
                  "source": "autotuner: 16-null probe batch, 8 candidates"}
+    null_model = 1 if args.null_model == "dyad" else 0
     if R:
-        batch = mt.Batch(dg, table, R, swaps, tuning)
+        batch = mt.Batch(dg, table, R, swaps, tuning, null_model=null_model)
         hists = torch.empty((R + 1, C), dtype=torch.int64, device="cuda")
         z = torch.empty(C, dtype=torch.float64, device="cuda")
 
@@ -376,7 +378,7 @@ def run_ours(args, world, rank, local):
 
     extra = {}
     if (rank == 0 and not args.no_extra and args.workload == "nullmodel_k5" and args.nulls is None
-            and args.method == "enumerate"):
+            and args.method == "enumerate" and args.null_model == "arcswap"):
         extra["plain_vs_batched"] = measure_plain_vs_batched(
             mt, torch, dg, table, g, (1 + R) / (total_ms / args.steps / 1000.0))
         extra["k3_uniform_latency"] = measure_single("uniform_k3", mt, torch)
@@ -735,6 +737,9 @@ def main():
                     help="skip the k=6 batch, plain-vs-batched and serving measurements")
     ap.add_argument("--compact-table", action="store_true",
                     help="k=6 only: count with the compact table (recorded in config)")
+    ap.add_argument("--null-model", default="arcswap", choices=["arcswap", "dyad"],
+                    help="null graphs by degree-preserving arc swaps (default) or dyad-preserving "
+                         "swaps (recorded in config)")
     ap.add_argument("--nulls", type=int, default=None,
                     help="number of null graphs (default: the workload's); smaller values make "
                          "the small cases profiled under ncu, recorded in config")

@@ -174,9 +174,15 @@ mt_status mt_table_entries(const mt_table* t, uint64_t first, uint64_t count, ui
  * gathered from the labelled neighbour rows (the row-scan strategy of Sec. 3.1)
  * and classified by one table read (Sec. 3.2).  n < k gives all zeros.
  * The call may grow device scratch memory held by the graph handle.
- * Errors: MT_EINVAL (null handle or hist), MT_EUNSUPPORTED (degree bound of the
- * device stack exceeded), MT_EOVERFLOW (device stack overflow detected, the
- * histogram is then invalid), MT_ENOMEM, MT_ECUDA. */
+ * Degree limit: each warp's candidate stack holds (k-2) * d + 32 vertex ids,
+ * d the largest undirected degree, and that must not exceed 65,535: d <=
+ * 65,503 / 32,751 / 21,834 / 16,375 for k = 3 / 4 / 5 / 6 (hubs of the
+ * "celebrity" graphs of Sec. 3.1).  Stacks too large for shared memory move
+ * to global memory (see mt_count_launch_info).
+ * Errors: MT_EINVAL (null handle or hist, or hist on another device than the
+ * current one), MT_EUNSUPPORTED (the degree limit above), MT_EOVERFLOW
+ * (device stack overflow detected, the histogram is then invalid),
+ * MT_ENOMEM, MT_ECUDA. */
 mt_status mt_count(const mt_graph* g, const mt_table* t, uint64_t* hist, void* stream);
 
 /* H_k restricted to the connected k-sets whose smallest vertex lies in
@@ -219,6 +225,19 @@ typedef struct {
   int stack_cap;
   int method;  /* mt_method */
 } mt_tuning;
+
+/* The automatic launch mt_count would make for `g` at k (host-side
+ * planning only, no device work): block size in warps, number of blocks (one
+ * persistent block per SM), candidate-stack entries per warp, and the memory
+ * layout as bits: 1 = the graph's CSR copied into shared memory, 2 = relation
+ * words in shared memory (else per-warp global slices), 4 = candidate stacks
+ * in per-warp global slices (chosen when shared-memory stacks would leave
+ * fewer than 16 warps, e.g. for hubs of thousands of neighbours).  Any output
+ * pointer may be NULL.  The paper has no counterpart.
+ * Errors: MT_EINVAL, MT_EUNSUPPORTED (k outside 3..6, or the degree limit of
+ * mt_count). */
+mt_status mt_count_launch_info(const mt_graph* g, int k, int32_t* warps_per_block,
+                               int32_t* blocks, int32_t* stack_cap, uint32_t* layout);
 
 /* mt_count with explicit tuning (`tuning` may be NULL = automatic).
  * Errors as mt_count, plus MT_EINVAL for out-of-range fields. */

@@ -63,6 +63,8 @@ SIGNATURES = {
     "mt_count_roots": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
     "mt_count_tuned": (ctypes.c_int, [_vp, _vp, _vp, _P(Tuning), _vp]),
     "mt_count_stats": (ctypes.c_int, [_vp, _P(_u64), _P(_u32), _P(ctypes.c_float)]),
+    "mt_count_launch_info": (ctypes.c_int, [_vp, ctypes.c_int, _P(_i32), _P(_i32), _P(_i32),
+                                            _P(_u32)]),
     "mt_count_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mt_count_noalloc_error": (ctypes.c_int, [_P(_u32), _vp]),
     "mt_workspace_query": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_size_t)]),
@@ -315,6 +317,15 @@ def count_noalloc_error(stream=None) -> int:
         raise MotifsError(st, "mt_count_noalloc_error", f"status word {err.value:#x}")
     _check(st, "mt_count_noalloc_error")
     return int(err.value)
+
+
+def launch_info(g: Graph, k: int) -> dict:
+    """The automatic counting launch for `g` at k (mt_count_launch_info)."""
+    w, b, cap, lay = _i32(), _i32(), _i32(), _u32()
+    _check(_lib.mt_count_launch_info(g.handle, int(k), w, b, cap, lay), "mt_count_launch_info")
+    return {"warps_per_block": w.value, "blocks": b.value, "stack_cap": cap.value,
+            "graph_in_smem": bool(lay.value & 1), "words_in_smem": bool(lay.value & 2),
+            "stacks_in_global": bool(lay.value & 4)}
 
 
 def workspace_query(g: Graph, k: int) -> int:

@@ -363,6 +363,7 @@ struct CountArgs {
   const uint16_t* xclass;    // compact k = 6 table: prefix key -> class of the first 4 vertices
   const uint8_t* xmap;       //   and its word relabelling (256 bytes per prefix key)
   void* lab_global;
+  void* stack_global;        // per-warp candidate stacks when they live in global memory
   int G, nmax, nu_cap, cap;
   uint32_t classes;
   int graph_bytes, hist_bytes, lab_bytes, buf_bytes, cell_bytes, map_bytes;
@@ -381,7 +382,9 @@ constexpr int kCells = 1 << (2 * (K - 2));
 // second-level choices as a new item.  When every warp is idle and nothing is
 // left to take, the block flushes its shared histogram, picks the next graph
 // that still has items and (GC) copies that graph's CSR into shared memory.
-template <int K, bool GC, bool LS, bool COMB>
+// SG: the candidate stacks live in per-warp slices of global memory (graphs
+// with hubs so large that shared-memory stacks would leave few warps).
+template <int K, bool GC, bool LS, bool COMB, bool SG = false>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_cur_g;
@@ -398,10 +401,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   sp += a.graph_bytes;
   int32_t* s_hist = (int32_t*)sp;
   sp += a.hist_bytes;
+  const int sbuf = SG ? 0 : a.buf_bytes;  // stack bytes in this warp's shared slice
   unsigned char* mine =
-      sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0) +
+      sp + (size_t)wid * ((LS ? a.lab_bytes : 0) + sbuf + (COMB ? a.cell_bytes : 0) +
                           kLevelBytes + a.map_bytes);
-  int* lvs = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + (COMB ? a.cell_bytes : 0));
+  int* lvs = (int*)(mine + (LS ? a.lab_bytes : 0) + sbuf + (COMB ? a.cell_bytes : 0));
   // compact k = 6 table: the current 4-vertex prefix's word relabelling
   uint8_t* xmw = (uint8_t*)lvs + kLevelBytes;
   const bool cpt = K == 6 && !COMB && a.xclass != nullptr;
@@ -410,13 +414,15 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   // multiple of 16), so 32-bit atomics on them are aligned
   LT* lab = LS ? (LT*)mine
                : (LT*)((char*)a.lab_global + ((size_t)blockIdx.x * nwarps + wid) * a.lab_bytes);
-  uint16_t* buf = (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
+  uint16_t* buf =
+      SG ? (uint16_t*)((char*)a.stack_global + ((size_t)blockIdx.x * nwarps + wid) * a.buf_bytes)
+         : (uint16_t*)(mine + (LS ? a.lab_bytes : 0));
   // combinatorial mode: per-cell counts (choices in the low, tail in the high
   // 16 bits), the list of non-empty cells, and its length
-  uint32_t* ct = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes);
+  uint32_t* ct = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + sbuf);
   uint16_t* cl = (uint16_t*)(ct + kCells<K>);
-  int* ncell = (int*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + a.cell_bytes - 16);
-  uint32_t* xc = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + a.buf_bytes + a.cell_bytes - 16 - 384);
+  int* ncell = (int*)(mine + (LS ? a.lab_bytes : 0) + sbuf + a.cell_bytes - 16);
+  uint32_t* xc = (uint32_t*)(mine + (LS ? a.lab_bytes : 0) + sbuf + a.cell_bytes - 16 - 384);
   const uint32_t C = a.classes;
 
   if (LS)
@@ -1026,22 +1032,24 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
 static size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 template <int K, bool CB>
-static const void* pick_kernel_kc(bool gc, bool ls) {
+static const void* pick_kernel_kc(bool gc, bool ls, bool sg) {
+  if (sg) return ls ? (const void*)k_count<K, false, true, CB, true>
+                    : (const void*)k_count<K, false, false, CB, true>;
   if (gc) return ls ? (const void*)k_count<K, true, true, CB> : (const void*)k_count<K, true, false, CB>;
   return ls ? (const void*)k_count<K, false, true, CB> : (const void*)k_count<K, false, false, CB>;
 }
 
 template <int K>
-static const void* pick_kernel_k(bool gc, bool ls, bool cb) {
-  return cb ? pick_kernel_kc<K, true>(gc, ls) : pick_kernel_kc<K, false>(gc, ls);
+static const void* pick_kernel_k(bool gc, bool ls, bool cb, bool sg) {
+  return cb ? pick_kernel_kc<K, true>(gc, ls, sg) : pick_kernel_kc<K, false>(gc, ls, sg);
 }
 
-static const void* pick_kernel(int K, bool gc, bool ls, bool cb) {
+static const void* pick_kernel(int K, bool gc, bool ls, bool cb, bool sg) {
   switch (K) {
-    case 3: return pick_kernel_k<3>(gc, ls, cb);
-    case 4: return pick_kernel_k<4>(gc, ls, cb);
-    case 5: return pick_kernel_k<5>(gc, ls, cb);
-    default: return pick_kernel_k<6>(gc, ls, cb);
+    case 3: return pick_kernel_k<3>(gc, ls, cb, sg);
+    case 4: return pick_kernel_k<4>(gc, ls, cb, sg);
+    case 5: return pick_kernel_k<5>(gc, ls, cb, sg);
+    default: return pick_kernel_k<6>(gc, ls, cb, sg);
   }
 }
 
@@ -1128,13 +1136,35 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
       }
     }
   }
+  // Graphs with hubs so large that no shared-memory layout holds 16 warps'
+  // candidate stacks: the stacks go to per-warp slices of global memory
+  // (L1/L2-cached), with the relation words in shared memory when they fit.
+  const size_t stack_bytes = round16((size_t)p->cap * 2);
+  p->stack_global = false;
+  if (!found || p->warps_per_block < std::min(want, 16)) {
+    int best_w = found ? p->warps_per_block : 0;
+    for (const bool ls : {true, false}) {
+      const size_t per = (ls ? lab_bytes : 0) + buf_bytes - stack_bytes;
+      int w = want;
+      while (w > 1 && hist_bytes + (size_t)w * per > budget) --w;
+      if (hist_bytes + (size_t)w * per <= budget && w > best_w) {
+        p->gcache = false;
+        p->lab_smem = ls;
+        p->stack_global = true;
+        p->warps_per_block = w;
+        p->smem_bytes = hist_bytes + (size_t)w * per;
+        found = true;
+        best_w = w;
+      }
+    }
+  }
   if (!found) return MT_EUNSUPPORTED;
   p->graph_bytes = p->gcache ? graph_bytes : 0;
   p->hist_bytes = hist_bytes;
   p->lab_bytes = lab_bytes;
   p->buf_bytes = buf_bytes - cell_bytes - kLevelBytes - p->map_bytes;
   p->cell_bytes = cell_bytes;
-  const void* kern = pick_kernel(K, p->gcache, p->lab_smem, p->comb);
+  const void* kern = pick_kernel(K, p->gcache, p->lab_smem, p->comb, p->stack_global);
   MT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)p->smem_bytes));
   int occ = 0;
@@ -1153,6 +1183,8 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
   p->off_items = off; off += round16(p->items_max * sizeof(Item));
   p->off_lab = off;
   if (!p->lab_smem) off += (size_t)p->blocks * p->warps_per_block * lab_bytes;
+  p->off_stack = off;
+  if (p->stack_global) off += (size_t)p->blocks * p->warps_per_block * p->buf_bytes;
   p->ws_bytes = off + 256;
   return MT_OK;
 }
@@ -1166,7 +1198,10 @@ uint32_t* count_nitems_ptr(const CountPlan& p, void* ws) {
 
 template <int K, bool CB>
 static void launch_count(const CountPlan& p, const CountArgs& a, unsigned threads, cudaStream_t s) {
-  if (p.gcache) {
+  if (p.stack_global) {
+    if (p.lab_smem) k_count<K, false, true, CB, true><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+    else k_count<K, false, false, CB, true><<<p.blocks, threads, p.smem_bytes, s>>>(a);
+  } else if (p.gcache) {
     if (p.lab_smem) k_count<K, true, true, CB><<<p.blocks, threads, p.smem_bytes, s>>>(a);
     else k_count<K, true, false, CB><<<p.blocks, threads, p.smem_bytes, s>>>(a);
   } else {
@@ -1218,6 +1253,7 @@ static cudaError_t enqueue_k(const CountPlan& p, void* ws, const DevGraph* graph
   a.map_bytes = (int)p.map_bytes;
   a.idle_ns = g_idle_ns;
   a.lab_global = lab;
+  a.stack_global = base + p.off_stack;
   a.G = p.G;
   a.nmax = p.nmax;
   a.nu_cap = p.nu_cap;
@@ -1372,6 +1408,21 @@ mt_status mt_workspace_query(const mt_graph* g, int k, size_t* bytes) {
   MT_TRY(count_configure_tuned(&p, k, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1),
                                kNumClasses[k], nullptr));
   *bytes = count_scratch_bytes(p, kNumClasses[k]);
+  return MT_OK;
+}
+
+mt_status mt_count_launch_info(const mt_graph* g, int k, int32_t* warps_per_block,
+                               int32_t* blocks, int32_t* stack_cap, uint32_t* layout) {
+  if (!g) return MT_EINVAL;
+  if (k < 3 || k > 6) return MT_EUNSUPPORTED;
+  CountPlan p;
+  MT_TRY(count_configure_tuned(&p, k, 1, g->n, g->dmax, g->nu / 2 + 1, std::max(g->nu, 1),
+                               kNumClasses[k], nullptr));
+  if (warps_per_block) *warps_per_block = p.warps_per_block;
+  if (blocks) *blocks = p.blocks;
+  if (stack_cap) *stack_cap = p.cap;
+  if (layout)
+    *layout = (p.gcache ? 1u : 0u) | (p.lab_smem ? 2u : 0u) | (p.stack_global ? 4u : 0u);
   return MT_OK;
 }
 

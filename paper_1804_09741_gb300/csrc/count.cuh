@@ -23,6 +23,7 @@ struct CountPlan {
   int blocks = 0;
   bool lab_smem = true;      // relation words in shared memory (else global slabs)
   bool gcache = true;        // the current graph's CSR copied into shared memory
+  bool stack_global = false; // candidate stacks in global memory (hub graphs)
   int nu_cap = 0;            // capacity of that copy (undirected entries)
   size_t graph_bytes = 0, hist_bytes = 0, lab_bytes = 0, buf_bytes = 0, cell_bytes = 0;
   bool comb = false;         // count the last two positions by cells (Algorithm 1)
@@ -38,6 +39,7 @@ struct CountPlan {
   size_t ws_bytes = 0;
   // workspace offsets
   size_t off_hdr = 0, off_qhead = 0, off_est = 0, off_cnt = 0, off_items = 0, off_lab = 0;
+  size_t off_stack = 0;
 };
 
 // Fill in the launch shape and the workspace size.  `fwd_bound` is a bound on

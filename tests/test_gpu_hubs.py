@@ -1,0 +1,115 @@
+"""Hubs of thousands of neighbours (the "celebrity" vertices of power-law
+graphs, Sec. 3.1): stars against the closed form C(d, k-1), and a hub inside a
+sparse background against oracle root samples that include the hub's
+neighbours.  Their candidate stacks ((k-2) d + 32 entries per warp) are too
+large for shared memory at a useful block size, so the launch keeps them in
+global memory; the tests check that layout is the one chosen.  GPU only."""
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from gpu_helpers import oracle_dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tables():
+    import paper_1804_09741_gb300 as mt
+    mt.load_library()
+    out = {}
+
+    def get(k):
+        if k not in out:
+            out[k] = mt.table_build(k)
+        return out[k]
+    yield get
+    for t in out.values():
+        t.free()
+
+
+def out_star(d):
+    return syn.csr_from_arcs(d + 1, np.zeros(d, np.int64), np.arange(1, d + 1), f"outstar({d})")
+
+
+def bidirected_star(d):
+    leaves = np.arange(1, d + 1)
+    return syn.csr_from_arcs(d + 1, np.concatenate([np.zeros(d, np.int64), leaves]),
+                             np.concatenate([leaves, np.zeros(d, np.int64)]), f"bistar({d})")
+
+
+def star_class(k, make):
+    """The canonical mask of the k-vertex star of the same orientation (oracle)."""
+    h, sets = oracle.count(make(k - 1), k)
+    assert sets == 1
+    return next(iter(h))
+
+
+@pytest.mark.parametrize("k,d,make", [(3, 4000, out_star), (4, 4000, out_star),
+                                      (4, 4000, bidirected_star), (5, 1000, out_star),
+                                      (6, 300, bidirected_star)])
+def test_star_hub_equals_closed_form(tables, k, d, make):
+    import paper_1804_09741_gb300 as mt
+    t = tables(k)
+    g = make(d)
+    dg = mt.graph_from(g)
+    assert dg.max_degree == d
+    info = mt.launch_info(dg, k)
+    if (k - 2) * d * 2 > 8192:  # stacks of more than 8 KB per warp
+        assert info["stacks_in_global"] and info["warps_per_block"] >= 16, info
+    h = mt.to_numpy_u64(mt.count(dg, t))
+    items, err, ms = mt.count_stats(dg)
+    assert err == 0
+    want = oracle_dense({star_class(k, make): comb(d, k - 1)}, t.class_masks())
+    np.testing.assert_array_equal(h, want)
+
+
+def hub_graph(n=5000, m=10000, d=4000, seed=11):
+    """A sparse Chung-Lu background on n-1 vertices plus a hub (the last
+    vertex) with arcs to and from d random others (a tenth of them mutual)."""
+    bg = syn.chung_lu_digraph(n - 1, m, 2.5, 30, 0.1, seed)
+    s, t = bg.arcs()
+    rng = np.random.default_rng(seed)
+    nb = rng.choice(n - 1, size=d, replace=False)
+    hub = n - 1
+    out_nb, in_nb = nb[: d // 2], nb[d // 2:]
+    mutual = nb[: d // 10]
+    src = np.concatenate([s, np.full(out_nb.size, hub), in_nb, mutual])
+    dst = np.concatenate([t, out_nb, np.full(in_nb.size, hub), np.full(mutual.size, hub)])
+    return syn.csr_from_arcs(n, src, dst, "hub+background"), np.sort(nb)
+
+
+def test_hub_in_background_matches_oracle_root_samples(tables):
+    import paper_1804_09741_gb300 as mt
+    k = 4
+    g, nb = hub_graph()
+    t = tables(k)
+    dg = mt.graph_from(g)
+    assert dg.max_degree >= 4000
+    info = mt.launch_info(dg, k)
+    assert info["stacks_in_global"] and info["warps_per_block"] >= 16, info
+    cm = t.class_masks()
+    # roots: three of the hub's neighbours (their sets through the hub are
+    # millions), forty low roots that are not, and the top of the id range
+    others = np.setdiff1d(np.arange(g.n - 1), nb)[:40]
+    samples = [np.array(nb[:3]), others, np.arange(g.n - 60, g.n)]
+    for roots in samples:
+        want, sets = oracle.count_roots_split(g, k, roots)
+        h = np.zeros(t.num_classes, np.uint64)
+        for r in roots:
+            h += mt.count_roots(dg, t, int(r), int(r) + 1)
+        assert int(h.sum()) == sets
+        np.testing.assert_array_equal(h, oracle_dense(want, cm))
+    # every root at once equals the sum over disjoint root ranges
+    full = mt.to_numpy_u64(mt.count(dg, t))
+    assert mt.count_stats(dg)[1] == 0
+    cuts = [0, int(nb[0]) + 1, 1000, 3000, g.n]
+    parts = sum(mt.count_roots(dg, t, cuts[i], cuts[i + 1]) for i in range(len(cuts) - 1))
+    np.testing.assert_array_equal(parts, full)
+    # the hub's own sets (hub is the largest id, so they belong to smaller
+    # roots): the number of connected 4-sets through the hub alone is at least
+    # C(d, 3)
+    assert int(full.sum()) >= comb(4000, 3)
