@@ -340,8 +340,8 @@ mt_status mt_randomize(const mt_graph* src, uint64_t seed, uint64_t swaps, void*
  * unless the entries coincide, a == c, b == d, a == d, c == b, or a new pair is
  * already adjacent in either direction.  In- and out-degrees, each vertex's
  * number of mutual partners and the dyad census are preserved.  Synchronises
- * `stream`.  Errors: MT_EINVAL, MT_EUNSUPPORTED (graph too large for the
- * on-chip arc set, m above about 17,000), MT_ENOMEM, MT_ECUDA. */
+ * `stream`.  Graphs whose arc set does not fit shared memory (m above about
+ * 17,000) keep it in global memory.  Errors: MT_EINVAL, MT_ENOMEM, MT_ECUDA. */
 mt_status mt_randomize_dyads(const mt_graph* src, uint64_t seed, uint64_t attempts, void* stream,
                              mt_graph** out);
 
@@ -364,8 +364,7 @@ typedef enum { MT_NULL_ARC_SWAP = 0, MT_NULL_DYAD_SWAP = 1 } mt_null_model;
 
 /* mt_batch_create with a choice of null model (an mt_null_model) and tuning
  * (NULL = automatic).  `swaps` is the number of attempts per null graph.
- * Errors: as mt_batch_create, MT_EUNSUPPORTED for a dyad model on a graph too
- * large for its on-chip arc set. */
+ * Errors: as mt_batch_create. */
 mt_status mt_batch_create_ex(const mt_graph* g, const mt_table* t, int R, uint64_t swaps,
                              int null_model, const mt_tuning* tuning, mt_batch** out);
 

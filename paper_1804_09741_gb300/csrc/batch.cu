@@ -21,8 +21,8 @@ cudaError_t launch_randomize(int32_t n, int32_t m, int G, const int32_t* row_ptr
 size_t rand_gscratch_words(int32_t m, int G);
 cudaError_t launch_randomize_dyads(int32_t n, int32_t m, int G, const int32_t* row_ptr,
                                    const int32_t* col0, const uint64_t* seeds, uint64_t attempts,
-                                   int32_t* col_out, int32_t* scratch, int64_t* accepted,
-                                   cudaStream_t s);
+                                   int32_t* col_out, int32_t* scratch, uint32_t* gscratch,
+                                   int64_t* accepted, cudaStream_t s);
 size_t dyad_scratch_ints(int32_t n, int32_t m);
 size_t rand_smem_bytes(int32_t m);
 }  // namespace mt
@@ -218,7 +218,7 @@ static mt_status batch_enqueue(mt_batch* b, cudaStream_t s) {
   MT_CUDA_TRY(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal));
   if (b->null_model == MT_NULL_DYAD_SWAP)
     MT_CUDA_TRY(launch_randomize_dyads(n, m, R, b->g0->row_ptr, b->g0->col, b->d_seeds, b->swaps,
-                                       b->col_rand, b->dyad_scratch, nullptr, s));
+                                       b->col_rand, b->dyad_scratch, b->rand_scratch, nullptr, s));
   else
     MT_CUDA_TRY(launch_randomize(n, m, R, b->g0->row_ptr, b->g0->col, b->d_seeds, b->swaps,
                                  b->col_rand, b->rand_scratch, nullptr, s));
@@ -309,7 +309,6 @@ mt_status mt_batch_create_ex(const mt_graph* g, const mt_table* t, int R, uint64
                  tuning->stack_cap < 0 || tuning->stack_cap > 65535 ||
                  tuning->method < 0 || tuning->method > 1))
     return MT_EINVAL;
-  if (null_model == MT_NULL_DYAD_SWAP && rand_smem_bytes(g->m) > 200 * 1024) return MT_EUNSUPPORTED;
   return batch_create(g, t, R, swaps, null_model, tuning, out);
 }
 

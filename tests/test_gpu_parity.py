@@ -317,6 +317,37 @@ def test_randomize_dyads_small_cases(lib):
             np.testing.assert_array_equal(col, ocol)
 
 
+@pytest.mark.parametrize("model", ["arcs", "dyads"])
+def test_randomize_large_graph_state_in_global_memory(lib, model):
+    """m = 50,000: the arc set does not fit shared memory, so the randomiser
+    keeps it in global memory; the null graph is still bit-exact (both null
+    models; the dyad one refused such graphs before)."""
+    g = syn.chung_lu_digraph(20000, 50000, 2.4, 200, 0.2, 21)
+    dg = lib.graph_from(g)
+    fn, ofn = ((lib.randomize, oracle.randomize) if model == "arcs"
+               else (lib.randomize_dyads, oracle.randomize_dyads))
+    r = fn(dg, 9, 10 * g.m)
+    rp, col = r.copy_csr()
+    orp, ocol, acc = ofn(g, 9, 10 * g.m)
+    assert acc > 0
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(col, ocol)
+
+
+def test_randomize_dense_graphs(lib):
+    """Complete and near-complete digraphs (most attempts rejected, buckets
+    full of structured keys), both null models, against the oracle."""
+    for g in [syn.complete_digraph(40), syn.random_small_digraph(60, 0.6, 0.5, 3)]:
+        dg = lib.graph_from(g)
+        for fn, ofn in [(lib.randomize, oracle.randomize),
+                        (lib.randomize_dyads, oracle.randomize_dyads)]:
+            r = fn(dg, 4, 10 * g.m)
+            rp, col = r.copy_csr()
+            orp, ocol, _ = ofn(g, 4, 10 * g.m)
+            np.testing.assert_array_equal(rp, orp)
+            np.testing.assert_array_equal(col, ocol)
+
+
 def test_duplicate_arc_rejected_on_device(lib):
     with pytest.raises(lib.MotifsError) as ei:
         lib.graph_load_csr(3, [0, 2, 2, 2], [1, 1])
