@@ -884,6 +884,30 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           // (b) the candidates after the group's first choice; those after
           //     choice g are its leaves, keyed by their word to the first k-2
           //     vertices plus slot g; equal keys of a batch share a table read
+          const int lc = e - c - 1;  // candidates after the group's first choice
+          if (lc <= 16 && ng > 1) {
+            // A short list: P choices per pass, 32 / P lanes each, every lane
+            // one (choice, candidate) pair; the match groups equal full keys,
+            // so pairs of different choices with the same key share a read.
+            const int P = lc <= 4 ? 8 : (lc <= 8 ? 4 : 2);
+            const int lw = P == 8 ? 2 : (P == 4 ? 3 : 4);  // log2 of the lanes per choice
+            const int h = lane >> lw, idx = lane & ((1 << lw) - 1);
+            const bool v0 = idx < lc;
+            const int u0 = v0 ? buf[c + 1 + idx] : 0;
+            const uint32_t lt = v0 ? (uint32_t)lab[u0] : 0u;
+            if (v0 && h == 0) lab[u0] = (LT)(lt & LM);
+            const uint32_t lb = cpt ? (uint32_t)xmw[lt & LM] : (lt & LM);
+            for (int p0 = 0; p0 < ng; p0 += P) {
+              const int gg = p0 + h;
+              const uint32_t pg = __shfl_sync(kFull, Pg, gg & 31);
+              const bool vg = v0 && gg < ng && idx + 1 > gg;
+              const uint32_t key = pg | ((lb | ((lt >> (2 * gg)) & (3u << NB))) << OFF1);
+              const unsigned peers = __match_any_sync(kFull, vg ? key : 0xFFFFFFFFu);
+              if (vg && !(peers & lanes_below)) ladd(__ldg(&a.table[key]), __popc(peers));
+            }
+            __syncwarp();
+            continue;
+          }
           uint32_t pgs[GS];
 #pragma unroll
           for (int gg = 0; gg < GS; ++gg) pgs[gg] = __shfl_sync(kFull, Pg, gg);

@@ -95,6 +95,27 @@ def test_table_k6_classes_and_sampled_keys(lib, tables):
     np.testing.assert_array_equal(block[ks[inblk].astype(np.int64)], want[order][inblk])
 
 
+def test_table_k6_ten_million_random_keys(lib, tables):
+    """10^7 random 6-vertex keys: the table's class id equals the oracle's
+    (brute-force canonical form over the 720 orderings, ranked among the class
+    masks), read back in 64 MB slices of the 4 GiB table."""
+    t = tables(6)
+    cm = t.class_masks()
+    rng = np.random.default_rng(7)
+    keys = np.unique(rng.integers(0, 1 << 30, size=10_000_000, dtype=np.uint64))
+    want = expected_ids(6, keys, cm)
+    got = np.empty(keys.size, np.uint32)
+    span = 1 << 24
+    starts = np.searchsorted(keys, np.arange(0, (1 << 30) + 1, span, dtype=np.uint64))
+    for i in range((1 << 30) // span):
+        a, b = starts[i], starts[i + 1]
+        if a == b:
+            continue
+        block = t.entries(i * span, span)
+        got[a:b] = block[(keys[a:b] - np.uint64(i * span)).astype(np.int64)]
+    np.testing.assert_array_equal(got, want)
+
+
 # ------------------------------------------------------------------ counting (K2)
 
 
