@@ -176,7 +176,6 @@ __device__ __forceinline__ bool swap_keys(const BucketSet& S, uint32_t n1, uint3
                         (v.z == kEmpty ? 4u : 0u) | (v.w == kEmpty ? 8u : 0u);
   const unsigned hm = __ballot_sync(kWarp, hit4 != 0);
   const unsigned em = __ballot_sync(kWarp, emp4 != 0);
-  const bool full = ((em >> (8 * grp)) & 0xFFu) == 0;
   const bool miss = ((hm >> (8 * grp)) & 0xFFu) == 0;
   // a key not in its home bucket may sit in a later one only past a flagged bucket
   const unsigned deeper = __ballot_sync(kWarp, sub == 0 && miss && S.overflowed(b));
@@ -216,7 +215,6 @@ __device__ __forceinline__ bool swap_keys(const BucketSet& S, uint32_t n1, uint3
   __syncwarp();
   ib1 = fast1 ? b1 : S.insert_warp(n1, lane);
   ib2 = fast2 ? b2 : S.insert_warp(n2, lane);
-  (void)full;
   return true;
 }
 
