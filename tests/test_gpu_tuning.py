@@ -44,6 +44,10 @@ def test_shallow_stack_is_reported(t5):
                                     None)
         mt._check(st, "mt_count_tuned")
     assert ei.value.status == mt.MT_EOVERFLOW
+    # the caller's retry with a deep enough stack (automatic: (k-2) d_max + 32) is exact
+    again = mt.to_numpy_u64(mt.count_tuned(dg, t5, 0.0, 8, stack_cap=0))
+    assert mt.count_stats(dg)[1] == 0
+    np.testing.assert_array_equal(again, mt.count_host(dg, t5))
 
 
 def test_batch_with_tuning_equals_default(t5):
