@@ -919,14 +919,38 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             if (v0) lab[u0] = (LT)(lt & LM);
             const int rel = v0 ? i0 - c : 0;  // candidate is after choice g iff rel > g
             const uint32_t lb = cpt ? (uint32_t)xmw[lt & LM] : (lt & LM);
+            // One match groups the lanes for M choices at once: the tag holds
+            // M fields of the leaf's word (NB + 2 bits) and a valid bit, and
+            // a group's leader classifies it for each choice it is a leaf of
+            // (M = 6, 4, 3, 2 for k = 3..6; at most 31 tag bits, so no valid
+            // tag is all ones).
+            constexpr int FB = NB + 3;
+            constexpr int M = (31 / FB) < GS ? (31 / FB) : GS;
 #pragma unroll
-            for (int gg = 0; gg < GS; ++gg) {
-              if (gg < ng) {
-                const bool vg = rel > gg;
-                const uint32_t wd = lb | ((lt >> (2 * gg)) & (3u << NB));
-                const unsigned peers = __match_any_sync(kFull, vg ? wd : 0xFFFFFFFFu);
-                if (vg && !(peers & lanes_below))
-                  ladd(__ldg(&a.table[pgs[gg] | (wd << OFF1)]), __popc(peers));
+            for (int g0 = 0; g0 < GS; g0 += M) {
+              if (g0 < ng) {
+                uint32_t tag = 0, wdv[M];
+                bool vv[M];
+                bool any = false;
+#pragma unroll
+                for (int t = 0; t < M; ++t) {
+                  const int gg = g0 + t;
+                  vv[t] = gg < ng && rel > gg;
+                  wdv[t] = lb | ((lt >> (2 * gg)) & (3u << NB));
+                  tag |= (vv[t] ? (wdv[t] | (1u << (NB + 2))) : 0u) << (FB * t);
+                  any |= vv[t];
+                }
+                const unsigned peers = __match_any_sync(kFull, any ? tag : 0xFFFFFFFFu);
+                if (any && !(peers & lanes_below)) {
+                  const int cnt = __popc(peers);
+                  uint32_t id[M];
+#pragma unroll
+                  for (int t = 0; t < M; ++t)
+                    id[t] = vv[t] ? __ldg(&a.table[pgs[(g0 + t) % GS] | (wdv[t] << OFF1)]) : 0u;
+#pragma unroll
+                  for (int t = 0; t < M; ++t)
+                    if (vv[t]) ladd(id[t], cnt);
+                }
               }
             }
           }
