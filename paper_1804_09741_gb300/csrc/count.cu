@@ -920,11 +920,12 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             const int rel = v0 ? i0 - c : 0;  // candidate is after choice g iff rel > g
             const uint32_t lb = cpt ? (uint32_t)xmw[lt & LM] : (lt & LM);
             // One match groups the lanes for M choices at once: the tag holds
-            // M fields of the leaf's word (NB + 2 bits) and a valid bit, and
-            // a group's leader classifies it for each choice it is a leaf of
-            // (M = 6, 4, 3, 2 for k = 3..6; at most 31 tag bits, so no valid
-            // tag is all ones).
-            constexpr int FB = NB + 3;
+            // M fields of NB + 2 bits, the leaf's word for a choice it is a
+            // leaf of and 0 otherwise (a candidate is adjacent to the first
+            // k-2 vertices, so its word is never 0), and a group's leader
+            // classifies it for each choice it is a leaf of (M = 3, 2, 3, 3
+            // for k = 3..6: at most 31 tag bits, so no tag is all ones).
+            constexpr int FB = NB + 2;
             constexpr int M = (31 / FB) < GS ? (31 / FB) : GS;
 #pragma unroll
             for (int g0 = 0; g0 < GS; g0 += M) {
@@ -937,7 +938,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
                   const int gg = g0 + t;
                   vv[t] = gg < ng && rel > gg;
                   wdv[t] = lb | ((lt >> (2 * gg)) & (3u << NB));
-                  tag |= (vv[t] ? (wdv[t] | (1u << (NB + 2))) : 0u) << (FB * t);
+                  tag |= (vv[t] ? wdv[t] : 0u) << (FB * t);
                   any |= vv[t];
                 }
                 const unsigned peers = __match_any_sync(kFull, any ? tag : 0xFFFFFFFFu);
