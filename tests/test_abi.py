@@ -82,8 +82,9 @@ def test_host_validation_rejects_malformed_csr(mtlib, case):
     assert _load(mtlib, n, rp, col) == 1  # MT_EINVAL
 
 
-def test_too_many_vertices_unsupported(mtlib):
-    n = 70000
+@pytest.mark.parametrize("n", [65536, 70000])
+def test_too_many_vertices_unsupported(mtlib, n):
+    """Vertex ids are 16 bits on the device: 65,535 vertices at most."""
     rp = np.zeros(n + 1, np.int32)
     col = np.zeros(1, np.int32)
     h = ctypes.c_void_p()

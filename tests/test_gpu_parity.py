@@ -253,6 +253,28 @@ def test_full_size_root_samples_and_partition(lib, tables, name):
     np.testing.assert_array_equal(cells, full)
 
 
+def test_largest_graph_the_loader_takes(lib, tables):
+    """n = 65,535, the most vertices a graph may have (ids are 16 bits in the
+    candidate stacks and in the randomiser's arc keys), relabelled so that the
+    hubs carry the highest ids: the whole k = 3 histogram and a k = 4 root
+    range against the oracle, and a null graph bit for bit."""
+    g0 = syn.chung_lu_digraph(65535, 130000, 2.5, 60, 0.15, 99)
+    g = syn.relabel(g0, np.arange(g0.n)[::-1])
+    dg = lib.graph_from(g)
+    assert dg.n == 65535
+    check_against_oracle(lib, tables(3), g, 3, via="device")
+    t4 = tables(4)
+    h = lib.count_roots(dg, t4, 30000, 30400)
+    want, sets = oracle.count_roots(g, 4, np.arange(30000, 30400))
+    assert sets > 0 and int(h.sum()) == sets
+    np.testing.assert_array_equal(h, oracle_dense(want, t4.class_masks()))
+    r = lib.randomize(dg, 5, 10 * g.m)
+    rp, col = r.copy_csr()
+    orp, ocol, _ = oracle.randomize(g, 5, 10 * g.m)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(col, ocol)
+
+
 def test_k5_workload_whole_graph_vs_oracle(lib, tables):
     """The whole k = 5 workload graph, hub roots included (the roots the
     enumerator splits into second-level items and donates between warps),
