@@ -48,10 +48,12 @@ def star_class(k, make):
     return next(iter(h))
 
 
+@pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("k,d,make", [(3, 4000, out_star), (4, 4000, out_star),
                                       (4, 4000, bidirected_star), (5, 1000, out_star),
                                       (6, 300, bidirected_star)])
-def test_star_hub_equals_closed_form(tables, k, d, make):
+def test_star_hub_equals_closed_form(tables, k, d, make, method):
+    """Both counting methods (per-subgraph classification and cell pairs)."""
     import paper_1804_09741_gb300 as mt
     t = tables(k)
     g = make(d)
@@ -60,7 +62,7 @@ def test_star_hub_equals_closed_form(tables, k, d, make):
     info = mt.launch_info(dg, k)
     if (k - 2) * d * 2 > 8192:  # stacks of more than 8 KB per warp
         assert info["stacks_in_global"] and info["warps_per_block"] >= 16, info
-    h = mt.to_numpy_u64(mt.count(dg, t))
+    h = mt.to_numpy_u64(mt.count_tuned(dg, t, method=method) if method else mt.count(dg, t))
     items, err, ms = mt.count_stats(dg)
     assert err == 0
     want = oracle_dense({star_class(k, make): comb(d, k - 1)}, t.class_masks())
