@@ -924,40 +924,28 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             if (v0) lab[u0] = (LT)(lt & LM);
             const int rel = v0 ? i0 - c : 0;  // candidate is after choice g iff rel > g
             const uint32_t lb = cpt ? (uint32_t)xmw[lt & LM] : (lt & LM);
-            // One match groups the lanes for M choices at once: the tag holds
-            // M fields of NB + 2 bits, the leaf's word for a choice it is a
-            // leaf of and 0 otherwise (a candidate is adjacent to the first
-            // k-2 vertices, so its word is never 0), and a group's leader
-            // classifies it for each choice it is a leaf of (M = 3, 2, 3, 3
-            // for k = 3..6: at most 31 tag bits, so no tag is all ones).
-            constexpr int FB = NB + 2;
-            constexpr int M = (31 / FB) < GS ? (31 / FB) : GS;
+            // One match groups the batch's lanes for every choice of the
+            // group: a leaf's key for choice g is a function of the
+            // candidate's relation word (its bits to the first k-2 vertices
+            // and the group's slot codes) and the candidate is a leaf of
+            // choices 0 .. vc-1, vc = min(ng, rel); lanes with equal word and
+            // vc have equal keys for every choice, and the leader of such a
+            // group classifies it for each of its vc choices.
+            constexpr int WB = NB + 2 * GS;  // relation-word bits in use (<= 24)
+            const uint32_t vc = (uint32_t)min(ng, rel);
+            const uint32_t tag = (lt & ((1u << WB) - 1u)) | (vc << WB);
+            const unsigned peers = __match_any_sync(kFull, vc ? tag : 0xFFFFFFFFu);
+            if (vc && !(peers & lanes_below)) {
+              const int cnt = __popc(peers);
+              uint32_t id[GS];
 #pragma unroll
-            for (int g0 = 0; g0 < GS; g0 += M) {
-              if (g0 < ng) {
-                uint32_t tag = 0, wdv[M];
-                bool vv[M];
-                bool any = false;
+              for (int gg = 0; gg < GS; ++gg)
+                id[gg] = gg < (int)vc
+                             ? __ldg(&a.table[pgs[gg] | ((lb | ((lt >> (2 * gg)) & (3u << NB))) << OFF1)])
+                             : 0u;
 #pragma unroll
-                for (int t = 0; t < M; ++t) {
-                  const int gg = g0 + t;
-                  vv[t] = gg < ng && rel > gg;
-                  wdv[t] = lb | ((lt >> (2 * gg)) & (3u << NB));
-                  tag |= (vv[t] ? wdv[t] : 0u) << (FB * t);
-                  any |= vv[t];
-                }
-                const unsigned peers = __match_any_sync(kFull, any ? tag : 0xFFFFFFFFu);
-                if (any && !(peers & lanes_below)) {
-                  const int cnt = __popc(peers);
-                  uint32_t id[M];
-#pragma unroll
-                  for (int t = 0; t < M; ++t)
-                    id[t] = vv[t] ? __ldg(&a.table[pgs[(g0 + t) % GS] | (wdv[t] << OFF1)]) : 0u;
-#pragma unroll
-                  for (int t = 0; t < M; ++t)
-                    if (vv[t]) ladd(id[t], cnt);
-                }
-              }
+              for (int gg = 0; gg < GS; ++gg)
+                if (gg < (int)vc) ladd(id[gg], cnt);
             }
           }
           __syncwarp();
