@@ -890,10 +890,12 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
           //     choice g are its leaves, keyed by their word to the first k-2
           //     vertices plus slot g; equal keys of a batch share a table read
           const int lc = e - c - 1;  // candidates after the group's first choice
-          if (lc <= 16 && ng > 1) {
-            // A short list: P choices per pass, 32 / P lanes each, every lane
-            // one (choice, candidate) pair; the match groups equal full keys,
-            // so pairs of different choices with the same key share a read.
+          if (K == 6 && lc <= 16 && ng > 1) {
+            // A short list (common at k = 6, where lists average 20
+            // candidates; measured no better at k = 5): P choices per pass,
+            // 32 / P lanes each, every lane one (choice, candidate) pair; the
+            // match groups equal full keys, so pairs of different choices with
+            // the same key share a read.
             const int P = lc <= 4 ? 8 : (lc <= 8 ? 4 : 2);
             const int lw = P == 8 ? 2 : (P == 4 ? 3 : 4);  // log2 of the lanes per choice
             const int h = lane >> lw, idx = lane & ((1 << lw) - 1);
