@@ -444,8 +444,8 @@ def _ceilings(mt, k, sub_rate, method="enumerate", workload=None):
     The kernel does not read the table once per subgraph: it reads once per
     group of equal keys.  So the reads and reductions it actually issues per
     classified subgraph come from an ncu capture of the current kernel
-    (global-load and global-reduction sectors of one small-case launch,
-    profiles/k_count_counters.json), and the fraction is issued sectors/s over
+    (global-load and global-reduction sectors of one launch of a smaller batch
+    that takes the same code path, profiles/k_count_counters.json), and the fraction is issued sectors/s over
     the probe's random reads/s (each probe read touches one sector)."""
     table_words = 1 << (k * (k - 1))
     hist_words = 1 << (int(syn_classes(k)) - 1).bit_length()
@@ -468,7 +468,7 @@ def _ceilings(mt, k, sub_rate, method="enumerate", workload=None):
     out["frac_of_gather"] = ld * sub_rate / gps
     out["frac_of_atomic"] = red * sub_rate / aps if red > 0 else 0.0
     out["note"] = ("issued global-load and global-reduction sectors per classified subgraph "
-                   "(ncu, small case of the same kernel) x the kernel's subgraphs/s, over the "
+                   "(ncu, a smaller batch on the same code path) x the kernel's subgraphs/s, over the "
                    "measured random-read and random-atomic rates (mt_probe_rates, this run); "
                    + cap.get("reading", ""))
     return out

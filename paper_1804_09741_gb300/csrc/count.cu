@@ -84,6 +84,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 constexpr int kMaxWarpsPerBlock = 32;
+// k = 6 launches with at most this many blocks per graph group a tail batch's
+// lanes with one match for all of a group's choices; launches over fewer graphs
+// match three choices at a time.  A block works on one graph at a time, so with
+// many blocks per graph many blocks add into the same global histogram, and the
+// finer groups of the single match (more leaders, each adding for every choice)
+// then queue on the same counters.  Measured on 152 blocks, k = 6 batches of
+// 2 .. 33 graphs run 22% .. 1.5% faster with three choices per match, 49 alike,
+// 65 3% slower.
+constexpr int kWideTailBlocksPerGraph = 3;
 // Per-warp stack of suspended DFS levels: (cursor, choice end, tail end, key, vertex).
 constexpr int kLevelBytes = 128;
 
@@ -414,6 +423,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
   // compact k = 6 table: the current 4-vertex prefix's word relabelling
   uint8_t* xmw = (uint8_t*)lvs + kLevelBytes;
   const bool cpt = K == 6 && !COMB && a.xclass != nullptr;
+  const bool wide_tail = K <= 5 || (int)gridDim.x <= kWideTailBlocksPerGraph * a.G;
   using LT = LabT<K, COMB>;
   // each warp's relation words start on a 16-byte boundary (lab_bytes is a
   // multiple of 16), so 32-bit atomics on them are aligned
@@ -926,28 +936,68 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_count(CountArgs a
             if (v0) lab[u0] = (LT)(lt & LM);
             const int rel = v0 ? i0 - c : 0;  // candidate is after choice g iff rel > g
             const uint32_t lb = cpt ? (uint32_t)xmw[lt & LM] : (lt & LM);
-            // One match groups the batch's lanes for every choice of the
-            // group: a leaf's key for choice g is a function of the
-            // candidate's relation word (its bits to the first k-2 vertices
-            // and the group's slot codes) and the candidate is a leaf of
-            // choices 0 .. vc-1, vc = min(ng, rel); lanes with equal word and
-            // vc have equal keys for every choice, and the leader of such a
-            // group classifies it for each of its vc choices.
-            constexpr int WB = NB + 2 * GS;  // relation-word bits in use (<= 24)
-            const uint32_t vc = (uint32_t)min(ng, rel);
-            const uint32_t tag = (lt & ((1u << WB) - 1u)) | (vc << WB);
-            const unsigned peers = __match_any_sync(kFull, vc ? tag : 0xFFFFFFFFu);
-            if (vc && !(peers & lanes_below)) {
-              const int cnt = __popc(peers);
-              uint32_t id[GS];
+            if (wide_tail) {
+              // One match groups the batch's lanes for every choice of the
+              // group (k <= 5, and k = 6 launches over many graphs).  A leaf's
+              // key for choice g is a function of the candidate's relation word
+              // (its bits to the first k-2 vertices and the group's slot
+              // codes), and the candidate is a leaf of choices 0 .. vc-1,
+              // vc = min(ng, rel); lanes with equal word and vc have equal keys
+              // for every choice, and the leader of such a group classifies it
+              // for each of its vc choices.
+              constexpr int WB = NB + 2 * GS;  // relation-word bits in use (<= 24)
+              const uint32_t vc = (uint32_t)min(ng, rel);
+              const uint32_t tag = (lt & ((1u << WB) - 1u)) | (vc << WB);
+              const unsigned peers = __match_any_sync(kFull, vc ? tag : 0xFFFFFFFFu);
+              if (vc && !(peers & lanes_below)) {
+                const int cnt = __popc(peers);
+                uint32_t id[GS];
 #pragma unroll
-              for (int gg = 0; gg < GS; ++gg)
-                id[gg] = gg < (int)vc
-                             ? __ldg(&a.table[pgs[gg] | ((lb | ((lt >> (2 * gg)) & (3u << NB))) << OFF1)])
-                             : 0u;
+                for (int gg = 0; gg < GS; ++gg)
+                  id[gg] = gg < (int)vc
+                               ? __ldg(&a.table[pgs[gg] | ((lb | ((lt >> (2 * gg)) & (3u << NB))) << OFF1)])
+                               : 0u;
 #pragma unroll
-              for (int gg = 0; gg < GS; ++gg)
-                if (gg < (int)vc) ladd(id[gg], cnt);
+                for (int gg = 0; gg < GS; ++gg)
+                  if (gg < (int)vc) ladd(id[gg], cnt);
+              }
+            } else {
+              // k = 6 over few graphs: one match groups the lanes for M = 3
+              // choices at once, so a leader adds for at most three.  The tag
+              // holds M fields of NB + 2 bits, the leaf's word for a choice it
+              // is a leaf of and 0 otherwise (a candidate is adjacent to the
+              // first k-2 vertices, so its word is never 0: at most 30 tag
+              // bits, so no tag is all ones), and a group's leader classifies
+              // it for each choice it is a leaf of.
+              constexpr int FB = NB + 2;
+              constexpr int M = (31 / FB) < GS ? (31 / FB) : GS;
+#pragma unroll
+              for (int g0 = 0; g0 < GS; g0 += M) {
+                if (g0 < ng) {
+                  uint32_t tag = 0, wdv[M];
+                  bool vv[M];
+                  bool any = false;
+#pragma unroll
+                  for (int t = 0; t < M; ++t) {
+                    const int gg = g0 + t;
+                    vv[t] = gg < ng && rel > gg;
+                    wdv[t] = lb | ((lt >> (2 * gg)) & (3u << NB));
+                    tag |= (vv[t] ? wdv[t] : 0u) << (FB * t);
+                    any |= vv[t];
+                  }
+                  const unsigned peers = __match_any_sync(kFull, any ? tag : 0xFFFFFFFFu);
+                  if (any && !(peers & lanes_below)) {
+                    const int cnt = __popc(peers);
+                    uint32_t id[M];
+#pragma unroll
+                    for (int t = 0; t < M; ++t)
+                      id[t] = vv[t] ? __ldg(&a.table[pgs[(g0 + t) % GS] | (wdv[t] << OFF1)]) : 0u;
+#pragma unroll
+                    for (int t = 0; t < M; ++t)
+                      if (vv[t]) ladd(id[t], cnt);
+                  }
+                }
+              }
             }
           }
           __syncwarp();

@@ -460,6 +460,61 @@ def test_batch_full_size_k5(lib, tables):
     np.testing.assert_array_equal(z, oracle.zscores(hists[0], hists[1:]))
 
 
+def test_batch_k6_many_graphs_vs_oracle(lib, tables):
+    """k = 6 over 64 graphs: with few blocks per graph the enumerator groups a
+    tail batch's leaves with one match for all choices (with many blocks per
+    graph, three choices per match); every row against the oracle's count of
+    the oracle's null graph."""
+    g = syn.chung_lu_digraph(60, 120, 2.3, None, 0.1, 106)
+    t = tables(6)
+    dg = lib.graph_from(g)
+    R = 63
+    roots = np.arange(g.n)
+    assert lib.launch_info(dg, 6)["blocks"] <= 3 * (R + 1)
+    seeds = np.arange(1, R + 1, dtype=np.uint64)
+    b = lib.Batch(dg, t, R, 10 * g.m)
+    hists, z = b.run(seeds)
+    hists = lib.to_numpy_u64(hists)
+    assert b.error() == 0
+    cm = t.class_masks()
+    np.testing.assert_array_equal(hists[0], oracle_dense(oracle.count_roots_split(g, 6, roots)[0], cm))
+    for r in range(R):
+        rp, col, _ = oracle.randomize(g, int(seeds[r]), 10 * g.m)
+        want, _ = oracle.count_roots_split(syn.Graph(g.n, rp, col), 6, roots)
+        np.testing.assert_array_equal(hists[r + 1], oracle_dense(want, cm))
+    np.testing.assert_array_equal(z.cpu().numpy(), oracle.zscores(hists[0], hists[1:]))
+
+
+def test_batch_full_size_k6(lib, tables):
+    """The k = 6 benchmark launch (original + 64 nulls, one launch, one match
+    per tail batch): sampled rows equal one-graph counts of the same null
+    graphs (launches of one graph, three choices per match) and the oracle on
+    root samples."""
+    name = "nullmodel_k6"
+    g = syn.workload_graph(name)
+    t = tables(6)
+    dg = lib.graph_from(g)
+    R = syn.WORKLOADS[name]["nulls"]
+    info = lib.launch_info(dg, 6)
+    assert 3 < info["blocks"] <= 3 * (R + 1)
+    seeds = np.arange(1, R + 1, dtype=np.uint64)
+    b = lib.Batch(dg, t, R, 10 * g.m)
+    hists, z = b.run(seeds)
+    hists = lib.to_numpy_u64(hists)
+    assert b.error() == 0
+    np.testing.assert_array_equal(hists[0], lib.to_numpy_u64(lib.count(dg, t)))
+    cm = t.class_masks()
+    for r in [0, 31, 63]:
+        nul = lib.randomize(dg, int(seeds[r]), 10 * g.m)
+        np.testing.assert_array_equal(hists[r + 1], lib.to_numpy_u64(lib.count(nul, t)))
+        if r == 63:
+            rp, col, _ = oracle.randomize(g, int(seeds[r]), 10 * g.m)
+            np.testing.assert_array_equal(nul.copy_csr()[1], col)
+            want, _ = oracle.count_roots(syn.Graph(g.n, rp, col), 6, np.arange(600, 640))
+            np.testing.assert_array_equal(lib.count_roots(nul, t, 600, 640), oracle_dense(want, cm))
+    np.testing.assert_array_equal(z.cpu().numpy(), oracle.zscores(hists[0], hists[1:]))
+
+
 @pytest.mark.parametrize("method", METHODS)
 def test_batch_dyad_null_model(lib, tables, method):
     """The batch with the dyad-preserving null model: rows equal the oracle's
