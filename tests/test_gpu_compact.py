@@ -130,6 +130,36 @@ def test_compact_full_size_workload(lib, tables):
                                   lib.to_numpy_u64(lib.count(dg, full)))
 
 
+def test_compact_batch_many_graphs(lib, tables):
+    """64 graphs in one launch (at most 3 blocks per graph: one match per tail
+    batch) with the compact table: rows equal the full table's batch, sampled
+    rows the oracle, and a few rows the one-graph counts (three choices per
+    match) with the compact table."""
+    full, compact = tables
+    g = syn.chung_lu_digraph(60, 120, 2.3, None, 0.1, 106)
+    dg = lib.graph_from(g)
+    R = 63
+    assert lib.launch_info(dg, 6)["blocks"] <= 3 * (R + 1)
+    seeds = np.arange(1, R + 1, dtype=np.uint64)
+    bc = lib.Batch(dg, compact, R, 10 * g.m)
+    hc, zc = bc.run(seeds)
+    hc, zc = lib.to_numpy_u64(hc), zc.cpu().numpy()
+    assert bc.error() == 0
+    bf = lib.Batch(dg, full, R, 10 * g.m)
+    hf, zf = bf.run(seeds)
+    np.testing.assert_array_equal(hc, lib.to_numpy_u64(hf))
+    np.testing.assert_array_equal(zc, zf.cpu().numpy())
+    bc.free()
+    bf.free()
+    cm = compact.class_masks()
+    for r in (0, 17, 62):
+        rp, col, _ = oracle.randomize(g, int(seeds[r]), 10 * g.m)
+        gr = syn.Graph(g.n, rp, col)
+        want, _ = oracle.count_roots_split(gr, 6, np.arange(g.n))
+        np.testing.assert_array_equal(hc[r + 1], oracle_dense(want, cm))
+        np.testing.assert_array_equal(hc[r + 1], lib.to_numpy_u64(lib.count(lib.graph_from(gr), compact)))
+
+
 def test_compact_rejects_cells_and_other_k(lib, tables):
     _, compact = tables
     g = syn.chung_lu_digraph(60, 150, 2.2, None, 0.1, 5)
