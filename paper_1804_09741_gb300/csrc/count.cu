@@ -29,10 +29,13 @@
 //    neighbours (their word is the arc code to the choice); then one pass over
 //    the remaining candidates classifies every choice's leaves from the words
 //    (key prefix OR word) and clears the slots again -- no per-subgraph
-//    adjacency test; one match_any groups the pass's lanes for several
-//    choices at once (their words packed in one tag), and a group of equal
-//    keys shares one table read; on short candidate lists several choices
-//    share one pass, a (choice, candidate) pair per lane;
+//    adjacency test; one match_any groups the pass's lanes for every choice
+//    at once (tag: the candidate's word, which fixes its key for each choice,
+//    plus the number of choices it is a leaf of), and a group of equal keys
+//    shares one table read; k = 6 launches with many blocks per graph match
+//    three choices at a time instead (kWideTailBlocksPerGraph); at k = 6,
+//    short candidate lists let several choices share one pass, a (choice,
+//    candidate) pair per lane;
 //  * MT_METHOD_CELLS stops one level earlier and counts the last two vertices
 //    per pair of cells (Algorithm 1 of Sec. 3; see pair_level below);
 //  * histograms: per-block shared-memory 32-bit counters for k <= 5 (13 / 199
@@ -43,10 +46,10 @@
 // branches, (graph, root, branch, second-level choice range); a planner sizes
 // them from per-branch cost estimates.  Hub graphs whose candidate stacks
 // ((k-2) x max degree + 32 entries per warp) would leave few warps in shared
-// memory keep the stacks in per-warp slices of global memory.  Blocks work graph by graph, warps take
-// the items of the block's current graph from that graph's queue, and a warp
-// that runs out takes halves of its block-mates' remaining ranges (work
-// donation).
+// memory keep the stacks in per-warp slices of global memory.  Blocks work
+// graph by graph, warps take the items of the block's current graph from that
+// graph's queue, and a warp that runs out takes halves of its block-mates'
+// remaining ranges (work donation).
 #include <algorithm>
 #include <type_traits>
 
