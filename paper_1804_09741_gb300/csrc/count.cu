@@ -33,7 +33,7 @@
 //    at once (tag: the candidate's word, which fixes its key for each choice,
 //    plus the number of choices it is a leaf of), and a group of equal keys
 //    shares one table read; k = 6 launches with many blocks per graph match
-//    three choices at a time instead (kWideTailBlocksPerGraph); at k = 6,
+//    three choices at a time instead (see kWideTailBlocksPerGraph); at k = 6,
 //    short candidate lists let several choices share one pass, a (choice,
 //    candidate) pair per lane;
 //  * MT_METHOD_CELLS stops one level earlier and counts the last two vertices
@@ -90,11 +90,11 @@ constexpr int kMaxWarpsPerBlock = 32;
 // k = 6 launches with at most this many blocks per graph group a tail batch's
 // lanes with one match for all of a group's choices; launches over fewer graphs
 // match three choices at a time.  A block works on one graph at a time, so with
-// many blocks per graph many blocks add into the same global histogram, and the
-// finer groups of the single match (more leaders, each adding for every choice)
-// then queue on the same counters.  Measured on 152 blocks, k = 6 batches of
-// 2 .. 33 graphs run 22% .. 1.5% faster with three choices per match, 49 alike,
-// 65 3% slower.
+// few graphs many blocks add into the same global histogram; there the single
+// match's finer groups (more leaders, each adding for every choice) sent 29%
+// more reduction sectors to L2 and ran slower.  Measured on 152 blocks, k = 6
+// batches of 2 .. 33 graphs run 22% .. 1.5% faster with three choices per
+// match, 49 alike, 65 3% slower.
 constexpr int kWideTailBlocksPerGraph = 3;
 // Per-warp stack of suspended DFS levels: (cursor, choice end, tail end, key, vertex).
 constexpr int kLevelBytes = 128;
