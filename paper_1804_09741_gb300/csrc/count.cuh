@@ -58,9 +58,14 @@ mt_status count_configure_tuned(CountPlan* p, int K, int G, int nmax, int dmax, 
 // Enqueue planner + enumerator.  `graphs` is a device array of G DevGraph whose
 // hist pointers are already zeroed (the launch adds into them).  Roots in
 // [root_begin, root_end) only.  No host synchronisation, no allocation.
+// `copies` > 1 (k = 6, G = 1 only): block b adds into copy b mod copies of the
+// graph's histogram, copy 0 being the graph's own and copy c >= 1 starting at
+// copies_base + (c - 1) * copy_stride (zeroed by the caller, folded by the
+// caller afterwards).
 mt_status count_enqueue(const CountPlan& p, void* ws, const DevGraph* graphs,
                         const TableView& table, int32_t root_begin, int32_t root_end,
-                        cudaStream_t s);
+                        cudaStream_t s, unsigned long long* copies_base = nullptr,
+                        int copies = 1, uint32_t copy_stride = 0);
 
 // Read the launch's error word and item count from the workspace (device
 // pointers into `ws`).  The header holding the error word is at offset 0 of
