@@ -173,7 +173,10 @@ mt_status mt_table_entries(const mt_table* t, uint64_t first, uint64_t count, ui
  * smallest vertex, extension by exclusive neighbours), its adjacency bits are
  * gathered from the labelled neighbour rows (the row-scan strategy of Sec. 3.1)
  * and classified by one table read (Sec. 3.2).  n < k gives all zeros.
- * The call may grow device scratch memory held by the graph handle.
+ * The call may grow device scratch memory held by the graph handle.  At k = 6
+ * that scratch includes 7 extra copies of the histogram (12 MB each): the
+ * count spreads its thread blocks over 8 copies, so that fewer blocks add into
+ * the same counters, and folds them into `hist` before it completes.
  * Degree limit: each warp's candidate stack holds (k-2) * d + 32 vertex ids,
  * d the largest undirected degree, and that must not exceed 65,535: d <=
  * 65,503 / 32,751 / 21,834 / 16,375 for k = 3 / 4 / 5 / 6 (hubs of the
@@ -285,7 +288,8 @@ mt_status mt_count_noalloc_error(uint32_t* err, void* stream);
  * counterpart; for callers whose device memory comes from their own allocator,
  * e.g. a torch tensor).  mt_workspace_query: the bytes of scratch that
  * mt_count / mt_count_roots of `g` at k need (automatic launch; a tuned launch
- * may need more).  Errors: MT_EINVAL, MT_EUNSUPPORTED (k outside 3..6).
+ * may need more; at k = 6 they include the histogram copies described at
+ * mt_count).  Errors: MT_EINVAL, MT_EUNSUPPORTED (k outside 3..6).
  * mt_set_workspace: attach `bytes` of DEVICE memory at `ws` (256-byte aligned;
  * the caller keeps ownership and must keep it alive until it is detached or
  * the graph is freed) as the scratch of every later count of `g`; those counts
